@@ -1,0 +1,598 @@
+/*
+ * ns_oracle.c -- FP64 CPU oracle for the hybrid SpMM C = A * B.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or load this file:
+ * only the tests, the package's smoke() check and the benchmark's CPU-baseline leg use it.
+ * It shares no code, header or table with the CUDA library; the two meet only in the seeded
+ * inputs drawn by the `synth` module.
+ *
+ * Two things live here:
+ *
+ *  1. orc_spmm_rows -- the plain definition of SpMM (Section 5.1, both execution models compute
+ *     the same product):  C[i,:] = sum_{p in row i} vals[p] * B[colidx[p], :], evaluated in
+ *     double precision with A's FP32 values and B's values (FP32, or BF16 widened exactly)
+ *     first widened to double, accumulated in ascending p.
+ *
+ *  2. orc_plan_build -- the CPU reference partition.  It takes the method's planning steps in
+ *     the paper's order (Section 5.2.2 row/column extraction with the Len rule of Eq. 4-5,
+ *     Section 6.1 row windows and column compaction, the tile density rule derived from the
+ *     cost model of Eq. 1-3, Section 7 row-window list balancing) with the integer readings
+ *     written down in the project design notes.  The device planner must reproduce every array
+ *     it emits bit for bit.
+ *
+ * Everything is deliberately simple: loops, qsort, binary search.  No blocking, no fusion.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_TAU_INF 2147483647
+
+/* ---------------------------------------------------------------------------------------- */
+/* scalar helpers                                                                            */
+/* ---------------------------------------------------------------------------------------- */
+
+static double orc_bf16_to_double(uint16_t h)
+{
+    uint32_t u = (uint32_t)h << 16; /* BF16 is the upper half of an IEEE-754 binary32 */
+    float f;
+    memcpy(&f, &u, sizeof f);
+    return (double)f;
+}
+
+/* Round-to-nearest-even of a binary32 to BF16 on the bit pattern: add 0x7FFF plus the
+ * lowest kept bit, then truncate.  Inputs carry no NaNs. */
+uint16_t orc_f32_to_bf16(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+void orc_f32_to_bf16_array(const float* x, int64_t count, uint16_t* out)
+{
+    for (int64_t i = 0; i < count; ++i) out[i] = orc_f32_to_bf16(x[i]);
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* 1. the SpMM definition                                                                    */
+/* ---------------------------------------------------------------------------------------- */
+
+/* C_out[r, :] = sum over row rows[r] of A, for r in [0, nrows).  B is n x K with leading
+ * dimension ldb (elements); b_bf16 selects uint16 BF16 storage.  C_out is nrows x K doubles. */
+int orc_spmm_rows(int32_t m, int32_t n, int32_t K, const int32_t* rowptr, const int32_t* colidx,
+                  const float* vals, const void* B, int32_t b_bf16, int64_t ldb,
+                  const int32_t* rows, int64_t nrows, double* C_out)
+{
+    if (K < 0 || ldb < K) return 1;
+    for (int64_t r = 0; r < nrows; ++r) {
+        int32_t i = rows[r];
+        double* c = C_out + r * (int64_t)K;
+        for (int32_t k = 0; k < K; ++k) c[k] = 0.0;
+        if (i < 0 || i >= m) return 1;
+        for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            int32_t j = colidx[p];
+            if (j < 0 || j >= n) return 1;
+            double a = (double)vals[p];
+            if (b_bf16) {
+                const uint16_t* b = (const uint16_t*)B + (int64_t)j * ldb;
+                for (int32_t k = 0; k < K; ++k) c[k] += a * orc_bf16_to_double(b[k]);
+            } else {
+                const float* b = (const float*)B + (int64_t)j * ldb;
+                for (int32_t k = 0; k < K; ++k) c[k] += a * (double)b[k];
+            }
+        }
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* 2. the reference partition                                                                */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t TM;          /* row-window height (Section 6.1: windows match the tile's M)         */
+    int32_t TK;          /* compacted columns per tile                                           */
+    int32_t tau_tile;    /* tile is dense iff tile_nnz >= tau_tile (alpha * TM * TK, rounded up) */
+    int32_t tau_row;     /* row goes to the residual iff Len(row) <= tau_row (Eq. 4-5)           */
+    int32_t tau_col;     /* column (inside the window rows) to residual iff count <= tau_col      */
+    int32_t col_order;   /* 0: count descending then column ascending; 1: column ascending       */
+    int32_t chunk_nnz;   /* W: merge items (residual nnz + row ends) per residual chunk           */
+    int32_t absorb_cap;  /* a dense window keeps its rows' residual if their nnz <= absorb_cap     */
+    int32_t group;       /* residual chunks per residual work item                               */
+    int32_t cost_tc;     /* Eq. 1 cost weight of one tile element                                */
+    int32_t cost_res;    /* Eq. 1 cost weight of one residual nonzero                            */
+} orc_tune;
+
+typedef struct {
+    int64_t m, n, nnz, K, b_bf16, TM, TK;
+    int64_t m_aic, n_win, n_dtiles, n_dwin, n_dvals, n_res, n_rl, T, n_chunks, n_split, n_slots,
+        n_items;
+    int32_t* aic_rows;
+    int32_t* win_rows;
+    int32_t* win_dptr;
+    int32_t* dwin;
+    int32_t* dwin_absorb;
+    int32_t* dtile_cols;
+    uint32_t* dtile_bits;
+    int32_t* dtile_voff;
+    void* dtile_vals;
+    int32_t* res_rowptr;
+    int32_t* res_col;
+    float* res_val;
+    int32_t* rl_rows;
+    int32_t* rl_start;
+    int32_t* chunk_b;
+    int32_t* chunk_k0;
+    int32_t* row_split;
+    int32_t* split_row;
+    int32_t* split_np;
+    int32_t* split_slot;
+    int32_t* split_fc;
+    int32_t* queue;
+    int64_t* item_cost;
+} orc_plan;
+
+typedef struct {
+    int32_t col, cnt;
+} orc_ucol;
+
+static int cmp_int32(const void* a, const void* b)
+{
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+static int cmp_ucol_count_desc(const void* a, const void* b)
+{
+    const orc_ucol* x = (const orc_ucol*)a;
+    const orc_ucol* y = (const orc_ucol*)b;
+    if (x->cnt != y->cnt) return (x->cnt < y->cnt) - (x->cnt > y->cnt);
+    return (x->col > y->col) - (x->col < y->col);
+}
+
+/* index of the largest k in [0, count) with arr[k] <= key (arr non-decreasing, arr[0] <= key) */
+static int64_t upper_minus_one(const int32_t* arr, int64_t count, int64_t key)
+{
+    int64_t lo = 0, hi = count; /* answer in [lo, hi) */
+    while (hi - lo > 1) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if ((int64_t)arr[mid] <= key) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+/* position of column j inside the sorted row segment colidx[b, e); -1 if absent */
+static int64_t find_in_row(const int32_t* colidx, int64_t b, int64_t e, int32_t j)
+{
+    while (b < e) {
+        int64_t mid = b + (e - b) / 2;
+        if (colidx[mid] == j) return mid;
+        if (colidx[mid] < j) b = mid + 1;
+        else e = mid;
+    }
+    return -1;
+}
+
+void orc_plan_free(orc_plan* p)
+{
+    if (!p) return;
+    free(p->aic_rows); free(p->win_rows); free(p->win_dptr); free(p->dwin); free(p->dwin_absorb);
+    free(p->dtile_cols); free(p->dtile_bits); free(p->dtile_voff); free(p->dtile_vals);
+    free(p->res_rowptr); free(p->res_col); free(p->res_val); free(p->rl_rows); free(p->rl_start);
+    free(p->chunk_b); free(p->chunk_k0); free(p->row_split); free(p->split_row);
+    free(p->split_np); free(p->split_slot); free(p->split_fc); free(p->queue); free(p->item_cost);
+    free(p);
+}
+
+/* growable buffer helper */
+static int grow(void** buf, int64_t* cap, int64_t need, size_t esize)
+{
+    if (need <= *cap) return 0;
+    int64_t nc = *cap ? *cap : 1024;
+    while (nc < need) nc *= 2;
+    void* nb = realloc(*buf, (size_t)nc * esize);
+    if (!nb) return 1;
+    *buf = nb;
+    *cap = nc;
+    return 0;
+}
+
+/* Returns 0 on success, 1 on an invalid CSR or tune, 2 on allocation failure. */
+int orc_plan_build(int32_t m, int32_t n, const int32_t* rowptr, const int32_t* colidx,
+                   const float* vals, int32_t K, int32_t b_bf16, const orc_tune* tu,
+                   orc_plan** out)
+{
+    *out = NULL;
+    /* ---- input checks: sorted unique in-range columns, monotone row pointers ---- */
+    if (m < 0 || n < 0 || K < 1) return 1;
+    if (rowptr[0] != 0) return 1;
+    for (int32_t i = 0; i < m; ++i) {
+        if (rowptr[i + 1] < rowptr[i]) return 1;
+        for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            if (colidx[p] < 0 || colidx[p] >= n) return 1;
+            if (p > rowptr[i] && colidx[p] <= colidx[p - 1]) return 1;
+        }
+    }
+    const int32_t TM = tu->TM, TK = tu->TK;
+    if (!(TM == 16 || TM == 32 || TM == 64) || !(TK == 16 || TK == 32)) return 1;
+    if (tu->chunk_nnz < 2 || tu->group < 1 || tu->cost_tc < 0 || tu->cost_res < 0) return 1;
+    const int64_t nnz = rowptr[m];
+    const int32_t BW = TM * TK / 32; /* bitmap words per tile */
+
+    orc_plan* P = (orc_plan*)calloc(1, sizeof(orc_plan));
+    if (!P) return 2;
+    P->m = m; P->n = n; P->nnz = nnz; P->K = K; P->b_bf16 = b_bf16 ? 1 : 0; P->TM = TM; P->TK = TK;
+
+    int32_t* len = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    uint8_t* is_dense_elem = (uint8_t*)calloc((size_t)(nnz > 0 ? nnz : 1), 1);
+    uint8_t* aic_col = (uint8_t*)malloc((size_t)(n > 0 ? n : 1));
+    if (!len || !is_dense_elem || !aic_col) { free(len); free(is_dense_elem); free(aic_col); orc_plan_free(P); return 2; }
+
+    /* ---- Eq. 4: Len(row); Eq. 5 rule with an integer threshold: row to residual iff
+     *      Len <= tau_row.  Windows (and with them the whole extraction) exist only when a
+     *      tile can be dense at all, i.e. tau_tile is finite. ---- */
+    for (int32_t i = 0; i < m; ++i) len[i] = rowptr[i + 1] - rowptr[i];
+    const int windows_on = tu->tau_tile != ORC_TAU_INF;
+    int64_t m_aic = 0;
+    if (windows_on)
+        for (int32_t i = 0; i < m; ++i) m_aic += len[i] > tu->tau_row;
+    P->m_aic = m_aic;
+    P->aic_rows = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m_aic > 0 ? m_aic : 1));
+    {
+        int64_t k = 0;
+        if (windows_on)
+            for (int32_t i = 0; i < m; ++i)
+                if (len[i] > tu->tau_row) P->aic_rows[k++] = i;
+    }
+
+    /* ---- second extraction stage: column lengths inside the rows kept for windows ---- */
+    for (int32_t j = 0; j < n; ++j) aic_col[j] = 1;
+    if (windows_on && tu->tau_col > 0) {
+        int32_t* colcount = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+        for (int64_t k = 0; k < m_aic; ++k) {
+            int32_t i = P->aic_rows[k];
+            for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) colcount[colidx[p]]++;
+        }
+        for (int32_t j = 0; j < n; ++j) aic_col[j] = colcount[j] > tu->tau_col;
+        free(colcount);
+    }
+
+    /* ---- windows: consecutive kept rows, TM per window, the last padded with -1 ---- */
+    const int64_t n_win = (m_aic + TM - 1) / TM;
+    P->n_win = n_win;
+    P->win_rows = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_win * TM > 0 ? n_win * TM : 1));
+    for (int64_t s = 0; s < n_win * TM; ++s) P->win_rows[s] = s < m_aic ? P->aic_rows[s] : -1;
+    P->win_dptr = (int32_t*)calloc((size_t)(n_win + 1), sizeof(int32_t));
+
+    /* growable outputs of the window pass */
+    int32_t* dcols = NULL; int64_t dcols_cap = 0;       /* n_dtiles * TK */
+    uint32_t* dbits = NULL; int64_t dbits_cap = 0;      /* n_dtiles * BW */
+    int32_t* dtnnz = NULL; int64_t dtnnz_cap = 0;       /* n_dtiles */
+    int64_t n_dt = 0;
+    int32_t* win_ntile_dense_rows = NULL; /* unused */
+    (void)win_ntile_dense_rows;
+
+    /* scratch per window */
+    int32_t* wcols = NULL; int64_t wcols_cap = 0;
+    orc_ucol* uc = NULL; int64_t uc_cap = 0;
+    int32_t* uasc = NULL; int64_t uasc_cap = 0;     /* ascending unique columns */
+    int32_t* upos = NULL; int64_t upos_cap = 0;     /* canonical position of each ascending entry */
+    int32_t* tile_rank = NULL; int64_t tile_rank_cap = 0; /* dense rank of tile t or -1 */
+
+    for (int64_t w = 0; w < n_win; ++w) {
+        /* collect the window's kept columns (Section 6.1: compaction drops empty columns) */
+        int64_t cnt = 0;
+        for (int32_t r = 0; r < TM; ++r) {
+            int32_t i = P->win_rows[w * TM + r];
+            if (i < 0) continue;
+            for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                if (!aic_col[colidx[p]]) continue;
+                if (grow((void**)&wcols, &wcols_cap, cnt + 1, sizeof(int32_t))) goto oom;
+                wcols[cnt++] = colidx[p];
+            }
+        }
+        qsort(wcols, (size_t)cnt, sizeof(int32_t), cmp_int32);
+        int64_t U = 0;
+        for (int64_t q = 0; q < cnt; ++q) {
+            if (q == 0 || wcols[q] != wcols[q - 1]) {
+                if (grow((void**)&uc, &uc_cap, U + 1, sizeof(orc_ucol))) goto oom;
+                uc[U].col = wcols[q];
+                uc[U].cnt = 1;
+                ++U;
+            } else {
+                uc[U - 1].cnt++;
+            }
+        }
+        if (grow((void**)&uasc, &uasc_cap, U + 1, sizeof(int32_t))) goto oom;
+        if (grow((void**)&upos, &upos_cap, U + 1, sizeof(int32_t))) goto oom;
+        for (int64_t q = 0; q < U; ++q) uasc[q] = uc[q].col;
+        /* canonical column order inside the window */
+        if (tu->col_order == 0) qsort(uc, (size_t)U, sizeof(orc_ucol), cmp_ucol_count_desc);
+        for (int64_t q = 0; q < U; ++q) {
+            int64_t a = find_in_row(uasc, 0, U, uc[q].col);
+            upos[a] = (int32_t)q;
+        }
+        /* tiles of TK consecutive positions; dense iff tile_nnz >= tau_tile */
+        int64_t ntile = (U + TK - 1) / TK;
+        if (grow((void**)&tile_rank, &tile_rank_cap, ntile + 1, sizeof(int32_t))) goto oom;
+        int64_t dt_begin = n_dt;
+        for (int64_t t = 0; t < ntile; ++t) {
+            int64_t tnnz = 0;
+            for (int64_t q = t * TK; q < (t + 1) * TK && q < U; ++q) tnnz += uc[q].cnt;
+            if (tnnz >= tu->tau_tile) {
+                tile_rank[t] = (int32_t)(n_dt - dt_begin);
+                if (grow((void**)&dcols, &dcols_cap, (n_dt + 1) * TK, sizeof(int32_t))) goto oom;
+                if (grow((void**)&dbits, &dbits_cap, (n_dt + 1) * BW, sizeof(uint32_t))) goto oom;
+                if (grow((void**)&dtnnz, &dtnnz_cap, n_dt + 1, sizeof(int32_t))) goto oom;
+                for (int32_t c = 0; c < TK; ++c) {
+                    int64_t q = t * TK + c;
+                    dcols[n_dt * TK + c] = q < U ? uc[q].col : -1;
+                }
+                for (int32_t b = 0; b < BW; ++b) dbits[n_dt * BW + b] = 0;
+                dtnnz[n_dt] = (int32_t)tnnz;
+                ++n_dt;
+            } else {
+                tile_rank[t] = -1;
+            }
+        }
+        P->win_dptr[w + 1] = (int32_t)n_dt;
+        /* mark each window element that fell into a dense tile and set its bitmap bit */
+        for (int32_t r = 0; r < TM; ++r) {
+            int32_t i = P->win_rows[w * TM + r];
+            if (i < 0) continue;
+            for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                if (!aic_col[colidx[p]]) continue;
+                int64_t a = find_in_row(uasc, 0, U, colidx[p]);
+                int32_t pos = upos[a];
+                int32_t t = pos / TK, c = pos % TK;
+                if (tile_rank[t] < 0) continue;
+                int64_t d = dt_begin + tile_rank[t];
+                int32_t bit = r * TK + c;
+                dbits[d * BW + bit / 32] |= 1u << (bit % 32);
+                is_dense_elem[p] = 1;
+            }
+        }
+    }
+    P->n_dtiles = n_dt;
+
+    /* ---- dense tile values, packed in bitmap order, each tile padded to 8 values ---- */
+    P->dtile_voff = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_dt + 1));
+    P->dtile_voff[0] = 0;
+    for (int64_t d = 0; d < n_dt; ++d)
+        P->dtile_voff[d + 1] = P->dtile_voff[d] + ((dtnnz[d] + 7) / 8) * 8;
+    P->n_dvals = P->dtile_voff[n_dt];
+    P->dtile_vals = calloc((size_t)(P->n_dvals > 0 ? P->n_dvals : 1), b_bf16 ? 2 : 4);
+    P->dtile_cols = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_dt * TK > 0 ? n_dt * TK : 1));
+    P->dtile_bits = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n_dt * BW > 0 ? n_dt * BW : 1));
+    if (n_dt) {
+        memcpy(P->dtile_cols, dcols, sizeof(int32_t) * (size_t)(n_dt * TK));
+        memcpy(P->dtile_bits, dbits, sizeof(uint32_t) * (size_t)(n_dt * BW));
+    }
+    for (int64_t w = 0; w < n_win; ++w) {
+        for (int64_t d = P->win_dptr[w]; d < P->win_dptr[w + 1]; ++d) {
+            int64_t v = P->dtile_voff[d];
+            for (int32_t bit = 0; bit < TM * TK; ++bit) {
+                if (!((P->dtile_bits[d * BW + bit / 32] >> (bit % 32)) & 1u)) continue;
+                int32_t r = bit / TK, c = bit % TK;
+                int32_t i = P->win_rows[w * TM + r];
+                int32_t j = P->dtile_cols[d * TK + c];
+                int64_t p = find_in_row(colidx, rowptr[i], rowptr[i + 1], j);
+                if (b_bf16) ((uint16_t*)P->dtile_vals)[v] = orc_f32_to_bf16(vals[p]);
+                else ((float*)P->dtile_vals)[v] = vals[p];
+                ++v;
+            }
+        }
+    }
+
+    /* ---- residual CSR: every element not in a dense tile, original rows, column order ---- */
+    P->res_rowptr = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    P->res_rowptr[0] = 0;
+    for (int32_t i = 0; i < m; ++i) {
+        int32_t c = 0;
+        for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) c += !is_dense_elem[p];
+        P->res_rowptr[i + 1] = P->res_rowptr[i] + c;
+    }
+    P->n_res = P->res_rowptr[m];
+    P->res_col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(P->n_res > 0 ? P->n_res : 1));
+    P->res_val = (float*)malloc(sizeof(float) * (size_t)(P->n_res > 0 ? P->n_res : 1));
+    {
+        int64_t z = 0;
+        for (int32_t i = 0; i < m; ++i)
+            for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+                if (!is_dense_elem[p]) { P->res_col[z] = colidx[p]; P->res_val[z] = vals[p]; ++z; }
+    }
+
+    /* ---- row ownership: dense windows own their rows; a dense window keeps (absorbs) its
+     *      rows' residual nonzeros when there are at most absorb_cap of them ---- */
+    int64_t n_dwin = 0;
+    for (int64_t w = 0; w < n_win; ++w) n_dwin += P->win_dptr[w + 1] > P->win_dptr[w];
+    P->n_dwin = n_dwin;
+    P->dwin = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_dwin > 0 ? n_dwin : 1));
+    P->dwin_absorb = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_dwin > 0 ? n_dwin : 1));
+    int8_t* row_state = (int8_t*)calloc((size_t)(m > 0 ? m : 1), 1); /* 0 free, 1 dense+absorb, 2 dense */
+    int64_t* dcost = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_dwin > 0 ? n_dwin : 1));
+    {
+        int64_t d = 0;
+        for (int64_t w = 0; w < n_win; ++w) {
+            if (P->win_dptr[w + 1] == P->win_dptr[w]) continue;
+            int64_t res_w = 0, nvalid = 0;
+            for (int32_t r = 0; r < TM; ++r) {
+                int32_t i = P->win_rows[w * TM + r];
+                if (i < 0) continue;
+                ++nvalid;
+                res_w += P->res_rowptr[i + 1] - P->res_rowptr[i];
+            }
+            int absorb = res_w <= tu->absorb_cap;
+            P->dwin[d] = (int32_t)w;
+            P->dwin_absorb[d] = absorb;
+            for (int32_t r = 0; r < TM; ++r) {
+                int32_t i = P->win_rows[w * TM + r];
+                if (i >= 0) row_state[i] = absorb ? 1 : 2;
+            }
+            int64_t ntd = P->win_dptr[w + 1] - P->win_dptr[w];
+            dcost[d] = ntd * TM * TK * (int64_t)tu->cost_tc + ((absorb ? res_w : 0) + nvalid) * (int64_t)tu->cost_res;
+            ++d;
+        }
+    }
+
+    /* ---- residual row list and merge-path chunks (Section 7, balanced lists) ---- */
+    int64_t n_rl = 0;
+    for (int32_t i = 0; i < m; ++i) {
+        int32_t rl = P->res_rowptr[i + 1] - P->res_rowptr[i];
+        if (row_state[i] == 0 || (row_state[i] == 2 && rl > 0)) ++n_rl;
+    }
+    P->n_rl = n_rl;
+    P->rl_rows = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_rl > 0 ? n_rl : 1));
+    P->rl_start = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_rl + 1));
+    {
+        int64_t k = 0;
+        P->rl_start[0] = 0;
+        for (int32_t i = 0; i < m; ++i) {
+            int32_t rl = P->res_rowptr[i + 1] - P->res_rowptr[i];
+            if (row_state[i] == 0 || (row_state[i] == 2 && rl > 0)) {
+                P->rl_rows[k] = i;
+                P->rl_start[k + 1] = P->rl_start[k] + rl + 1;
+                ++k;
+            }
+        }
+    }
+    const int64_t T = P->rl_start[n_rl];
+    const int64_t W = tu->chunk_nnz;
+    P->T = T;
+    const int64_t nc = T > 0 ? (T + W - 1) / W : 0;
+    P->n_chunks = nc;
+    P->chunk_b = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nc + 1));
+    P->chunk_k0 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nc > 0 ? nc : 1));
+    P->chunk_b[0] = 0;
+    for (int64_t c = 1; c < nc; ++c) {
+        int64_t dgn = c * W;
+        int64_t k = upper_minus_one(P->rl_start, n_rl, dgn);
+        int64_t rlen = P->res_rowptr[P->rl_rows[k] + 1] - P->res_rowptr[P->rl_rows[k]];
+        P->chunk_b[c] = (int32_t)((2 * (rlen + 1) <= W) ? P->rl_start[k] : dgn);
+    }
+    if (nc > 0) P->chunk_b[nc] = (int32_t)T;
+    for (int64_t c = 0; c < nc; ++c)
+        P->chunk_k0[c] = (int32_t)upper_minus_one(P->rl_start, n_rl, P->chunk_b[c]);
+
+    /* ---- pieces per row; rows with two or more pieces are split rows ---- */
+    int32_t* npieces = (int32_t*)calloc((size_t)(m > 0 ? m : 1), sizeof(int32_t));
+    int32_t* firstc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    for (int32_t i = 0; i < m; ++i) { npieces[i] = row_state[i] ? 1 : 0; firstc[i] = -1; }
+    for (int64_t k = 0; k < n_rl; ++k) {
+        int32_t i = P->rl_rows[k];
+        int64_t fc = upper_minus_one(P->chunk_b, nc, P->rl_start[k]);
+        int64_t lc = upper_minus_one(P->chunk_b, nc, (int64_t)P->rl_start[k + 1] - 1);
+        npieces[i] += (int32_t)(lc - fc + 1);
+        firstc[i] = (int32_t)fc;
+    }
+    int64_t n_split = 0;
+    for (int32_t i = 0; i < m; ++i) n_split += npieces[i] >= 2;
+    P->n_split = n_split;
+    P->row_split = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    P->split_row = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_split > 0 ? n_split : 1));
+    P->split_np = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_split > 0 ? n_split : 1));
+    P->split_slot = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_split > 0 ? n_split : 1));
+    P->split_fc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_split > 0 ? n_split : 1));
+    {
+        int64_t s = 0, slot = 0;
+        for (int32_t i = 0; i < m; ++i) {
+            if (npieces[i] >= 2) {
+                P->row_split[i] = (int32_t)s;
+                P->split_row[s] = i;
+                P->split_np[s] = npieces[i];
+                P->split_slot[s] = (int32_t)slot;
+                P->split_fc[s] = firstc[i];
+                slot += npieces[i];
+                ++s;
+            } else {
+                P->row_split[i] = -1;
+            }
+        }
+        P->n_slots = slot;
+    }
+
+    /* ---- work items and their order: cost classes (floor log2 of the Eq. 1 cost) from
+     *      heaviest to lightest, then item id; dense items come before residual items ---- */
+    const int64_t G = tu->group;
+    const int64_t nq = (nc + G - 1) / G;
+    const int64_t n_items = n_dwin + nq;
+    P->n_items = n_items;
+    P->queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_items > 0 ? n_items : 1));
+    P->item_cost = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_items > 0 ? n_items : 1));
+    for (int64_t d = 0; d < n_dwin; ++d) P->item_cost[d] = dcost[d];
+    for (int64_t q = 0; q < nq; ++q) {
+        int64_t c1 = (q + 1) * G < nc ? (q + 1) * G : nc;
+        P->item_cost[n_dwin + q] = ((int64_t)P->chunk_b[c1] - P->chunk_b[q * G]) * tu->cost_res;
+    }
+    {
+        int64_t k = 0;
+        for (int bucket = 62; bucket >= 0; --bucket)
+            for (int64_t it = 0; it < n_items; ++it) {
+                int64_t c = P->item_cost[it];
+                int b = 0;
+                while (b < 62 && (c >> (b + 1)) > 0) ++b; /* floor(log2(c)), 0 for c <= 1 */
+                if (b == bucket) P->queue[k++] = (int32_t)it;
+            }
+    }
+
+    free(npieces); free(firstc); free(row_state); free(dcost);
+    free(len); free(is_dense_elem); free(aic_col);
+    free(dcols); free(dbits); free(dtnnz); free(wcols); free(uc); free(uasc); free(upos); free(tile_rank);
+    *out = P;
+    return 0;
+
+oom:
+    free(len); free(is_dense_elem); free(aic_col);
+    free(dcols); free(dbits); free(dtnnz); free(wcols); free(uc); free(uasc); free(upos); free(tile_rank);
+    orc_plan_free(P);
+    return 2;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* accessors for the Python wrapper                                                          */
+/* ---------------------------------------------------------------------------------------- */
+
+int64_t orc_plan_scalar(const orc_plan* P, const char* name)
+{
+#define S(x) if (!strcmp(name, #x)) return P->x;
+    S(m) S(n) S(nnz) S(K) S(b_bf16) S(TM) S(TK) S(m_aic) S(n_win) S(n_dtiles) S(n_dwin) S(n_dvals)
+    S(n_res) S(n_rl) S(T) S(n_chunks) S(n_split) S(n_slots) S(n_items)
+#undef S
+    return -1;
+}
+
+/* ptr, element count and element size (bytes) of a named array; returns 1 if unknown */
+int orc_plan_array(const orc_plan* P, const char* name, const void** ptr, int64_t* count,
+                   int32_t* esize)
+{
+    const int64_t TM = P->TM, TK = P->TK, BW = TM * TK / 32;
+#define A(x, cnt, es) if (!strcmp(name, #x)) { *ptr = P->x; *count = (cnt); *esize = (es); return 0; }
+    A(aic_rows, P->m_aic, 4)
+    A(win_rows, P->n_win * TM, 4)
+    A(win_dptr, P->n_win + 1, 4)
+    A(dwin, P->n_dwin, 4)
+    A(dwin_absorb, P->n_dwin, 4)
+    A(dtile_cols, P->n_dtiles * TK, 4)
+    A(dtile_bits, P->n_dtiles * BW, 4)
+    A(dtile_voff, P->n_dtiles + 1, 4)
+    A(dtile_vals, P->n_dvals, P->b_bf16 ? 2 : 4)
+    A(res_rowptr, P->m + 1, 4)
+    A(res_col, P->n_res, 4)
+    A(res_val, P->n_res, 4)
+    A(rl_rows, P->n_rl, 4)
+    A(rl_start, P->n_rl + 1, 4)
+    A(chunk_b, P->n_chunks + 1, 4)
+    A(chunk_k0, P->n_chunks, 4)
+    A(row_split, P->m, 4)
+    A(split_row, P->n_split, 4)
+    A(split_np, P->n_split, 4)
+    A(split_slot, P->n_split, 4)
+    A(split_fc, P->n_split, 4)
+    A(queue, P->n_items, 4)
+    A(item_cost, P->n_items, 8)
+#undef A
+    return 1;
+}

@@ -1,0 +1,243 @@
+/*
+ * ns_spmm.h -- C ABI of the GB300 hybrid sparse x dense matrix multiply.
+ *
+ * Operation (Section 5.1 of arXiv 2606.22482, "NeutronSparse"):  C = A * B, where A is an
+ * m x n sparse matrix in CSR form, B an n x K dense matrix and C the m x K dense result.  The
+ * method splits A into dense row-window tiles, run on the matrix engine (here: the tensor
+ * cores), and a sparse residual, run on the vector engine (here: the CUDA cores), and runs both
+ * from one balanced work list (Sections 5.2, 6 and 7).
+ *
+ * Conventions shared by every entry point
+ *  - All functions return an ns_status_t and never abort the process.  On failure a message is
+ *    available from ns_last_error() (thread-local, valid until the next call on that thread).
+ *  - Streams are cudaStream_t passed as void*; NULL means the legacy default stream.  Work is
+ *    enqueued on the stream; ns_spmm_plan and ns_autotune synchronise it before returning.
+ *  - Dense matrices are row-major with a leading dimension in elements (ldb >= K, ldc >= K).
+ *    Device pointers to B and C must be 16-byte aligned and ldb, ldc multiples of 8.
+ *  - Kernels never trap.  A kernel that detects an internal error or gives up a bounded wait
+ *    writes a device status word; the next call on the same object reports it.
+ *  - Indices are int32; nnz < 2^31.  m, n < 2^31.
+ */
+#ifndef NS_SPMM_H
+#define NS_SPMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NS_OK = 0,
+    NS_ERR_INVALID = 1,     /* bad argument or invalid CSR (unsorted/duplicate/out-of-range column,
+                               non-monotone row pointers) */
+    NS_ERR_UNSUPPORTED = 2, /* valid but not handled: K % 8 != 0, K > 1024, unaligned B/C */
+    NS_ERR_OOM = 3,         /* device or host allocation failed */
+    NS_ERR_CUDA = 4,        /* a CUDA runtime call failed; message names it */
+    NS_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    NS_ERR_AGAIN = 6,       /* serving: queue full, retry later */
+    NS_ERR_TOO_LARGE = 7,   /* serving: request footprint exceeds the HBM budget */
+    NS_ERR_NOT_FOUND = 8    /* unknown array name / ticket */
+} ns_status_t;
+
+/* Storage type of B.  C is always FP32.  NS_BF16 also stores dense-tile values of A in BF16
+ * (round to nearest even) and runs those tiles on the tensor cores in BF16 with FP32
+ * accumulation; the residual always runs in FP32 with B widened exactly. */
+typedef enum { NS_F32 = 0, NS_BF16 = 1 } ns_dtype_t;
+
+typedef void* ns_stream_t;
+
+/* A CSR matrix.  Columns must be sorted ascending and unique inside each row (explicit zeros
+ * are structure).  on_device = 1: the three arrays are device pointers that the caller keeps
+ * alive and unchanged until every plan made from them is destroyed (plans may reference them);
+ * on_device = 0: host arrays, copied during ns_spmm_plan. */
+typedef struct {
+    int32_t m, n;
+    int64_t nnz;
+    const int32_t* rowptr; /* m + 1 entries, rowptr[0] = 0, rowptr[m] = nnz */
+    const int32_t* colidx; /* nnz entries */
+    const float* vals;     /* nnz entries */
+    int32_t on_device;
+} ns_csr_t;
+
+#define NS_TAU_INF 2147483647
+
+/* Planner and execution parameters (Sections 5.2 and 6.2).  Fill with ns_tune_default() and
+ * change fields, or let ns_autotune() choose them.
+ *   TM          row-window height: 16, 32 or 64 rows (Section 6.1 windows match the tile's M)
+ *   TK          compacted columns per dense tile: 16 or 32
+ *   tau_tile    a tile is dense iff its nonzero count >= tau_tile; the integer form of the
+ *               density threshold alpha of Eq. 3 (tau = ceil(alpha * TM * TK)).  NS_TAU_INF:
+ *               no dense tiles (pure CUDA-core path); <= 1: every compacted tile is dense
+ *   tau_row     row extraction (Eq. 4-5): a row with Len <= tau_row goes straight to the residual
+ *   tau_col     column extraction inside the kept rows: a column with count <= tau_col goes
+ *               to the residual (0 disables the stage)
+ *   col_order   order of compacted columns inside a window: 0 count-descending then column,
+ *               1 column-ascending
+ *   chunk_nnz   W, residual merge items (nonzeros + row ends) per warp chunk
+ *   absorb_cap  a dense window also computes its rows' residual when that has <= absorb_cap nnz
+ *   group       residual chunks per work item (one per warp of the execute CTA; must be 4)
+ *   cost_tc     Eq. 1 weight of one dense-tile element in the work-list order
+ *   cost_res    Eq. 1 weight of one residual merge item in the work-list order
+ *   l2_hints    1: stream A and C with evict-first and keep B with evict-last L2 policies
+ *               (Section 6.2.1 hot-B staging, in GPU form); 0: default caching */
+typedef struct {
+    int32_t TM, TK, tau_tile, tau_row, tau_col, col_order, chunk_nnz, absorb_cap, group,
+        cost_tc, cost_res, l2_hints;
+} ns_tune_t;
+
+void ns_tune_default(ns_tune_t* t);
+
+/* Counts of a plan, named as in the CPU reference partition. */
+typedef struct {
+    int64_t m, n, nnz, K, b_bf16, TM, TK;
+    int64_t m_aic;    /* rows kept for windows after row extraction */
+    int64_t n_win;    /* row windows */
+    int64_t n_dtiles; /* dense tiles */
+    int64_t n_dwin;   /* windows with at least one dense tile (dense work items) */
+    int64_t n_dvals;  /* stored dense-tile values incl. padding to 8 per tile */
+    int64_t n_res;    /* residual nonzeros */
+    int64_t n_rl;     /* rows handled by residual chunks */
+    int64_t T;        /* residual merge items */
+    int64_t n_chunks; /* residual warp chunks */
+    int64_t n_split;  /* rows assembled from several pieces */
+    int64_t n_slots;  /* partial-row slots */
+    int64_t n_items;  /* work items of the execute launch */
+} ns_plan_stats_t;
+
+typedef struct ns_plan* ns_plan_t;
+
+/* Build the execution plan of A for dense operands of width K and type b_dtype (Sections 4,
+ * 5.2.2, 6.1, 7): validates A, extracts short rows/columns, forms TM-row windows, compacts
+ * their columns into TK-wide tiles, bins tiles by density against tau_tile, builds the residual
+ * CSR, splits it into nnz-balanced chunks and orders all work items by estimated cost.  Every
+ * step runs as device kernels on `s`; the call synchronises `s` (plan sizes are data-dependent).
+ * tune == NULL uses ns_tune_default().  The plan owns its device arrays until ns_plan_destroy.
+ * Errors: NS_ERR_INVALID (bad CSR or tune), NS_ERR_UNSUPPORTED (K), NS_ERR_OOM, NS_ERR_CUDA. */
+ns_status_t ns_spmm_plan(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, const ns_tune_t* tune,
+                         ns_stream_t s, ns_plan_t* out);
+
+/* C := A * B (overwrite; every row of C is written) with one persistent launch over the plan's
+ * work list (Section 5.1 execution models, Section 7 balanced lists).  B (n x K, b_dtype) and
+ * C (m x K, FP32) are device pointers owned by the caller.  Asynchronous on `s`.  Plans are
+ * not re-entrant: at most one execute of a given plan may be in flight.
+ * Errors: NS_ERR_INVALID, NS_ERR_UNSUPPORTED (alignment), NS_ERR_TIMEOUT / NS_ERR_CUDA from a
+ * previous launch of this plan, NS_ERR_CUDA. */
+ns_status_t ns_spmm_execute(ns_plan_t p, const void* B, int64_t ldb, float* C, int64_t ldc,
+                            ns_stream_t s);
+
+/* One-shot C = A * B from HOST memory: copies A (host CSR), B (host, n x K) to the device, plans,
+ * executes and copies C (host, m x K) back, all on `s`; returns after `s` is synchronised.
+ * Pinned host buffers give the fastest copies.  Device buffers are cached inside the library
+ * between calls (freed by ns_release_cache).  Same errors as plan + execute. */
+ns_status_t ns_spmm_host(const ns_csr_t* A, const void* B, int32_t K, ns_dtype_t b_dtype,
+                         float* C, const ns_tune_t* tune, ns_stream_t s);
+ns_status_t ns_release_cache(void);
+
+ns_status_t ns_plan_stats(ns_plan_t p, ns_plan_stats_t* st);
+
+/* Copy one named plan array to host memory (for bit-exact comparison with the CPU reference
+ * partition).  Names: aic_rows win_rows win_dptr dwin dwin_absorb dtile_cols dtile_bits
+ * dtile_voff dtile_vals res_rowptr res_col res_val rl_rows rl_start chunk_b chunk_k0 row_split
+ * split_row split_np split_slot split_fc queue item_cost.  ns_plan_array_info gives the element
+ * count and size; `bytes` must be at least count * esize.  Synchronous. */
+ns_status_t ns_plan_array_info(ns_plan_t p, const char* name, int64_t* count, int32_t* esize);
+ns_status_t ns_plan_export(ns_plan_t p, const char* name, void* host_dst, int64_t bytes);
+
+ns_status_t ns_plan_destroy(ns_plan_t p);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Batched form: many independent SpMMs in one persistent launch, replayed from a CUDA graph. */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct ns_batch* ns_batch_t;
+
+/* Plan `count` matrices (each with its own K) and merge their work lists into one.  The batch
+ * owns the plans.  Errors as ns_spmm_plan; on error nothing is kept. */
+ns_status_t ns_batch_plan(const ns_csr_t* As, int32_t count, const int32_t* Ks, ns_dtype_t b_dtype,
+                          const ns_tune_t* tune, ns_stream_t s, ns_batch_t* out);
+
+/* C_g := A_g * B_g for every g, in ONE persistent kernel launch.  The launch is captured into a
+ * CUDA graph on the first call and replayed afterwards; the operand table is refreshed by one
+ * host-to-device copy when pointers change.  Bs[g], Cs[g] are device pointers, ldb = ldc = K_g. */
+ns_status_t ns_batch_execute(ns_batch_t b, const void* const* Bs, float* const* Cs, ns_stream_t s);
+ns_status_t ns_batch_stats(ns_batch_t b, int64_t* n_items, int64_t* n_graphs);
+ns_status_t ns_batch_destroy(ns_batch_t b);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Autotuner (Section 5.2.1 dry run + Section 8 sweeps).                                     */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct {
+    double p_res;     /* measured residual throughput, nonzeros * K per second            */
+    double p_tc;      /* measured dense-tile throughput, tile elements * K per second     */
+    double alpha0;    /* Eq. 3 with r = 1: p_res / p_tc                                    */
+    double best_ms;   /* execute time of the chosen tune                                    */
+    int32_t trials;   /* configurations timed                                               */
+} ns_tune_report_t;
+
+/* Dry-run microbenchmarks on A (or on synthetic tiles when A is small) give p_res and p_tc,
+ * hence alpha0 and tau0 = ceil(alpha0 * TM * TK); then (TM, tau) candidates around tau0 plus the
+ * two single-engine extremes are planned and timed, and the fastest is returned in *out.
+ * A must be on the device.  Synchronous; report may be NULL. */
+ns_status_t ns_autotune(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, ns_stream_t s,
+                        ns_tune_t* out, ns_tune_report_t* report);
+
+/* Host-side helpers of the cost model (pure functions, no GPU needed). */
+double ns_cost_alpha(double p_res, double p_tc, double r);            /* Eq. 3 */
+int32_t ns_cost_tau(double alpha, int32_t TM, int32_t TK);           /* ceil(alpha*TM*TK) */
+double ns_skew(double dt_tc, double dt_res);                         /* Eq. 6 */
+
+/* ---------------------------------------------------------------------------------------- */
+/* Serving: continuous batching of SpMM requests on one GPU.                                 */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct ns_server* ns_server_t;
+
+typedef struct {
+    int64_t hbm_budget_bytes; /* admission limit for resident plans + operands                 */
+    int32_t max_inflight;     /* requests admitted at once (slots)                               */
+    int32_t max_queue;        /* requests waiting for admission before NS_ERR_AGAIN             */
+    int32_t max_graphs;       /* resident graph plans kept (LRU beyond)                          */
+    ns_tune_t tune;           /* tune used for every plan                                        */
+} ns_serve_cfg_t;
+
+/* A request: graph_id names a graph registered with ns_serve_register_graph; B and C are host
+ * pointers (row-major, ld = K) that stay valid until the request is reported done. */
+typedef struct {
+    int32_t graph_id;
+    int32_t K;
+    ns_dtype_t b_dtype;
+    const void* B;
+    float* C;
+    double t_arrival; /* caller's clock (seconds) at which the request arrived; for latency */
+} ns_request_t;
+
+typedef struct {
+    double t_admit, t_start, t_done; /* seconds on the server clock (ns_serve_now) */
+    int32_t status;                  /* ns_status_t of the request                  */
+} ns_req_stats_t;
+
+ns_status_t ns_serve_create(const ns_serve_cfg_t* cfg, ns_server_t* out);
+/* Register a host CSR graph; the server copies it.  Returns its id in *graph_id. */
+ns_status_t ns_serve_register_graph(ns_server_t sv, const ns_csr_t* A, int32_t* graph_id);
+/* Queue a request; returns immediately.  NS_ERR_AGAIN if the queue is full, NS_ERR_TOO_LARGE if
+ * the request could never fit the HBM budget. */
+ns_status_t ns_serve_submit(ns_server_t sv, const ns_request_t* r, uint64_t* ticket);
+/* Non-blocking completion check; *done = 1 once C has been written to the host buffer. */
+ns_status_t ns_serve_poll(ns_server_t sv, uint64_t ticket, int* done, ns_req_stats_t* st);
+double ns_serve_now(void);
+ns_status_t ns_serve_destroy(ns_server_t sv);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Diagnostics                                                                               */
+/* ---------------------------------------------------------------------------------------- */
+const char* ns_last_error(void);
+/* Kernels launched by this library in this process (all entry points). */
+int64_t ns_launch_count(void);
+/* 1 if the library was built for the device it runs on (sm_103a), else 0. */
+int32_t ns_device_ok(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NS_SPMM_H */

@@ -42,7 +42,7 @@ DEFAULT_TUNE = dict(TM=16, TK=16, tau_tile=TAU_INF, tau_row=0, tau_col=0, col_or
 PLAN_ARRAYS = ("aic_rows", "win_rows", "win_dptr", "dwin", "dwin_absorb", "dtile_cols",
                "dtile_bits", "dtile_voff", "dtile_vals", "res_rowptr", "res_col", "res_val",
                "rl_rows", "rl_start", "chunk_b", "chunk_k0", "row_split", "split_row",
-               "split_np", "split_slot", "split_fc", "queue", "item_cost")
+               "split_np", "split_slot", "split_base", "queue", "item_cost")
 PLAN_SCALARS = ("m", "n", "nnz", "K", "b_bf16", "TM", "TK", "m_aic", "n_win", "n_dtiles",
                 "n_dwin", "n_dvals", "n_res", "n_rl", "T", "n_chunks", "n_split", "n_slots",
                 "n_items")

@@ -126,13 +126,13 @@ def plan(A: dict, K: int, *, b_bf16: bool = False, **tune) -> dict:
         first_chunk[i] = min(chunks)
     split = [i for i in range(m) if pieces.get(i, 0) >= 2]
     row_split = [-1] * m
-    split_np, split_slot, split_fc = [], [], []
+    split_np, split_slot, split_base = [], [], []
     slot = 0
     for s, i in enumerate(split):
         row_split[i] = s
         split_np.append(pieces[i])
         split_slot.append(slot)
-        split_fc.append(first_chunk[i])
+        split_base.append(first_chunk[i] - (1 if i in owner else 0))
         slot += pieces[i]
 
     G = t["group"]
@@ -159,6 +159,6 @@ def plan(A: dict, K: int, *, b_bf16: bool = False, **tune) -> dict:
         res_val=np.asarray([x for r in res for _, x in r], dtype=np.float32),
         rl_rows=i32(rl), rl_start=i32(starts), chunk_b=i32(bounds if nc else [0]),
         chunk_k0=i32(chunk_k0), row_split=i32(row_split), split_row=i32(split),
-        split_np=i32(split_np), split_slot=i32(split_slot), split_fc=i32(split_fc),
+        split_np=i32(split_np), split_slot=i32(split_slot), split_base=i32(split_base),
         queue=i32(queue), item_cost=np.asarray(costs, dtype=np.int64),
     )

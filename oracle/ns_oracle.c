@@ -129,7 +129,7 @@ typedef struct {
     int32_t* split_row;
     int32_t* split_np;
     int32_t* split_slot;
-    int32_t* split_fc;
+    int32_t* split_base;
     int32_t* queue;
     int64_t* item_cost;
 } orc_plan;
@@ -183,7 +183,7 @@ void orc_plan_free(orc_plan* p)
     free(p->dtile_cols); free(p->dtile_bits); free(p->dtile_voff); free(p->dtile_vals);
     free(p->res_rowptr); free(p->res_col); free(p->res_val); free(p->rl_rows); free(p->rl_start);
     free(p->chunk_b); free(p->chunk_k0); free(p->row_split); free(p->split_row);
-    free(p->split_np); free(p->split_slot); free(p->split_fc); free(p->queue); free(p->item_cost);
+    free(p->split_np); free(p->split_slot); free(p->split_base); free(p->queue); free(p->item_cost);
     free(p);
 }
 
@@ -495,7 +495,7 @@ int orc_plan_build(int32_t m, int32_t n, const int32_t* rowptr, const int32_t* c
     P->split_row = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_split > 0 ? n_split : 1));
     P->split_np = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_split > 0 ? n_split : 1));
     P->split_slot = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_split > 0 ? n_split : 1));
-    P->split_fc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_split > 0 ? n_split : 1));
+    P->split_base = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_split > 0 ? n_split : 1));
     {
         int64_t s = 0, slot = 0;
         for (int32_t i = 0; i < m; ++i) {
@@ -504,7 +504,8 @@ int orc_plan_build(int32_t m, int32_t n, const int32_t* rowptr, const int32_t* c
                 P->split_row[s] = i;
                 P->split_np[s] = npieces[i];
                 P->split_slot[s] = (int32_t)slot;
-                P->split_fc[s] = firstc[i];
+                /* chunk c delivers piece c - split_base; a dense window, if any, piece 0 */
+                P->split_base[s] = firstc[i] - (row_state[i] ? 1 : 0);
                 slot += npieces[i];
                 ++s;
             } else {
@@ -590,7 +591,7 @@ int orc_plan_array(const orc_plan* P, const char* name, const void** ptr, int64_
     A(split_row, P->n_split, 4)
     A(split_np, P->n_split, 4)
     A(split_slot, P->n_split, 4)
-    A(split_fc, P->n_split, 4)
+    A(split_base, P->n_split, 4)
     A(queue, P->n_items, 4)
     A(item_cost, P->n_items, 8)
 #undef A

@@ -1,0 +1,157 @@
+"""Python binding of libns_spmm (GB300 hybrid tensor-core / CUDA-core SpMM).
+
+Argument marshalling only: every step of planning and execution runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  The names mirror the C ABI in
+``include/ns_spmm.h``; importing fails loudly when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _abi
+from ._abi import (NS_F32, NS_BF16, NS_TAU_INF, NsError, Tune, PlanStats, lib, check,
+                   tune_default)
+
+__all__ = ["NS_F32", "NS_BF16", "NS_TAU_INF", "NsError", "Tune", "PlanStats", "Plan",
+           "spmm_plan", "spmm_execute", "spmm_host", "tune_default", "launch_count", "lib",
+           "PLAN_ARRAYS"]
+
+PLAN_ARRAYS = ("aic_rows", "win_rows", "win_dptr", "dwin", "dwin_absorb", "dtile_cols",
+               "dtile_bits", "dtile_voff", "dtile_vals", "res_rowptr", "res_col", "res_val",
+               "rl_rows", "rl_start", "chunk_b", "chunk_k0", "row_split", "split_row",
+               "split_np", "split_slot", "split_base", "queue", "item_cost")
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _csr_struct(A, device: bool) -> tuple[_abi.Csr, list]:
+    """ns_csr_t from a dict with torch tensors (device) or numpy arrays (host); keeps refs."""
+    keep = []
+    if device:
+        rp, ci, v = A["rowptr"], A["colidx"], A["vals"]
+        for t, dt in ((rp, "int32"), (ci, "int32"), (v, "float32")):
+            if not t.is_cuda or not t.is_contiguous() or str(t.dtype) != f"torch.{dt}":
+                raise NsError(1, f"device CSR arrays must be contiguous CUDA {dt} tensors")
+        ptrs = (rp.data_ptr(), ci.data_ptr(), v.data_ptr())
+        keep += [rp, ci, v]
+        nnz = int(ci.numel())
+    else:
+        rp = np.ascontiguousarray(A["rowptr"], dtype=np.int32)
+        ci = np.ascontiguousarray(A["colidx"], dtype=np.int32)
+        v = np.ascontiguousarray(A["vals"], dtype=np.float32)
+        keep += [rp, ci, v]
+        ptrs = (rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+        nnz = int(ci.size)
+    c = _abi.Csr(int(A["m"]), int(A["n"]), nnz, ctypes.c_void_p(ptrs[0]), ctypes.c_void_p(ptrs[1]),
+                 ctypes.c_void_p(ptrs[2]), 1 if device else 0)
+    return c, keep
+
+
+class Plan:
+    """An execution plan (owns its device arrays until closed)."""
+
+    def __init__(self, handle, keep, K: int, dtype: int):
+        self._h = handle
+        self._keep = keep
+        self.K = K
+        self.dtype = dtype
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> dict:
+        st = PlanStats()
+        check(lib.ns_plan_stats(self._h, ctypes.byref(st)))
+        return {f: int(getattr(st, f)) for f, _ in PlanStats._fields_}
+
+    def export(self, name: str) -> np.ndarray:
+        cnt = ctypes.c_int64()
+        es = ctypes.c_int32()
+        check(lib.ns_plan_array_info(self._h, name.encode(), ctypes.byref(cnt), ctypes.byref(es)))
+        if name == "dtile_vals":
+            dt = np.uint16 if es.value == 2 else np.float32
+        elif name == "dtile_bits":
+            dt = np.uint32
+        elif name == "res_val":
+            dt = np.float32
+        elif name == "item_cost":
+            dt = np.int64
+        else:
+            dt = np.int32
+        out = np.empty(int(cnt.value), dtype=dt)
+        check(lib.ns_plan_export(self._h, name.encode(), out.ctypes.data_as(ctypes.c_void_p),
+                                 out.nbytes))
+        return out
+
+    def execute(self, B, C, stream=None) -> None:
+        """C := A @ B on the device (B: n x K float32 or bfloat16 tensor, C: m x K float32)."""
+        spmm_execute(self, B, C, stream)
+
+    def close(self) -> None:
+        if self._h:
+            check(lib.ns_plan_destroy(self._h))
+            self._h = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def spmm_plan(A: dict, K: int, b_dtype: int = NS_F32, tune: Tune | None = None, *,
+              device: bool | None = None, stream=None) -> Plan:
+    """ns_spmm_plan.  ``A`` holds torch CUDA tensors (device CSR, referenced by the plan) or
+    numpy arrays (host CSR, copied)."""
+    if device is None:
+        device = hasattr(A["rowptr"], "is_cuda") and A["rowptr"].is_cuda
+    c, keep = _csr_struct(A, device)
+    h = ctypes.c_void_p()
+    check(lib.ns_spmm_plan(ctypes.byref(c), int(K), int(b_dtype),
+                           ctypes.byref(tune) if tune is not None else None,
+                           _stream_handle(stream), ctypes.byref(h)))
+    return Plan(h, keep if device else None, int(K), int(b_dtype))
+
+
+def spmm_execute(plan: Plan, B, C, stream=None) -> None:
+    """ns_spmm_execute with torch CUDA tensors."""
+    import torch
+    if not (B.is_cuda and C.is_cuda) or C.dtype != torch.float32:
+        raise NsError(1, "B and C must be CUDA tensors, C float32")
+    if (plan.dtype == NS_BF16) != (B.dtype == torch.bfloat16):
+        raise NsError(1, "B dtype does not match the plan")
+    ldb = B.stride(0) if B.dim() == 2 else plan.K
+    ldc = C.stride(0) if C.dim() == 2 else plan.K
+    check(lib.ns_spmm_execute(plan.handle, ctypes.c_void_p(B.data_ptr()), int(ldb),
+                              ctypes.c_void_p(C.data_ptr()), int(ldc), _stream_handle(stream)))
+
+
+def spmm_host(A: dict, B: np.ndarray, C: np.ndarray, b_dtype: int = NS_F32,
+              tune: Tune | None = None, stream=None) -> None:
+    """ns_spmm_host: C = A @ B with every operand in host memory (copies inside the call)."""
+    c, keep = _csr_struct(A, False)
+    K = int(B.shape[1])
+    assert C.dtype == np.float32 and C.flags["C_CONTIGUOUS"] and B.flags["C_CONTIGUOUS"]
+    check(lib.ns_spmm_host(ctypes.byref(c), ctypes.c_void_p(B.ctypes.data), K, int(b_dtype),
+                           ctypes.c_void_p(C.ctypes.data),
+                           ctypes.byref(tune) if tune is not None else None,
+                           _stream_handle(stream)))
+
+
+def launch_count() -> int:
+    return int(lib.ns_launch_count())

@@ -1,0 +1,454 @@
+// ns_plan.cu -- the device-side planner (Sections 4, 5.2.2, 6.1 and 7 of arXiv 2606.22482).
+//
+// Turns a CSR matrix into the execution plan consumed by the persistent kernel:
+//   a1  validate + row lengths Len (Eq. 4)
+//   a2  row extraction: Len <= tau_row -> residual (Eq. 5 with an integer threshold)
+//   a3  column extraction inside the kept rows: count <= tau_col -> residual
+//   a4  row windows of TM consecutive kept rows (Section 6.1)
+//   a5  column compaction per window, canonical column order, TK-wide tiles
+//   a6  density binning: tile dense iff nnz >= tau_tile (alpha of Eq. 3 as an integer)
+//   a7  residual CSR of everything not in a dense tile
+//   a8  merge-path chunks of the residual with short rows never cut
+//   a9  work items ordered by cost class (Eq. 1), heaviest first (Section 7 balanced lists)
+// Every array is defined exactly like the CPU reference partition; the tests compare them bit
+// for bit.  All arithmetic is integer; all reductions have a fixed order.
+#include "ns_internal.cuh"
+#include "ns_scan.cuh"
+
+namespace ns {
+
+// ---------------------------------------------------------------------------------------------
+// a1: validation without per-row loops.  Inside a row columns must strictly increase, so every
+// position p where colidx[p+1] <= colidx[p] ("descent") must be a row start.  Counting all
+// descents (element-parallel) and the descents that sit at row starts (row-parallel) and
+// comparing the two counts checks sortedness and uniqueness of every row.
+// ---------------------------------------------------------------------------------------------
+enum { kCtrTicket = 0, kCtrDone = 1, kCtrStatus = 2 };
+// 64-bit counters used by the planner
+enum { kCnBadRange = 0, kCnDescents = 1, kCnBadPtr = 2, kCnStartDescents = 3, kCnTotals = 4 };
+
+__global__ void k_check_elems(const int32_t* __restrict__ colidx, int64_t nnz, int32_t n,
+                              unsigned long long* cnt)
+{
+    unsigned long long bad = 0, desc = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int32_t c = __ldg(colidx + p);
+        bad += (c < 0 || c >= n);
+        if (p + 1 < nnz) desc += (__ldg(colidx + p + 1) <= c);
+    }
+    bad = warp_sum(bad);
+    desc = warp_sum(desc);
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicAdd(cnt + kCnBadRange, bad);
+        if (desc) atomicAdd(cnt + kCnDescents, desc);
+    }
+}
+
+__global__ void k_check_rows(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                             int32_t m, int64_t nnz, unsigned long long* cnt)
+{
+    unsigned long long bad = 0, sdesc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = __ldg(rowptr + i);
+        bool ok = r >= 0 && r <= nnz;
+        if (i == 0 && r != 0) ok = false;
+        if (i == m && r != nnz) ok = false;
+        if (i < m) {
+            int64_t r1 = __ldg(rowptr + i + 1);
+            if (r1 < r) ok = false;
+            // a non-empty row starting after position 0: is its start a descent?
+            if (ok && r1 > r && r > 0 && r < nnz) sdesc += (__ldg(colidx + r) <= __ldg(colidx + r - 1));
+        }
+        bad += !ok;
+    }
+    bad = warp_sum(bad);
+    sdesc = warp_sum(sdesc);
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicAdd(cnt + kCnBadPtr, bad);
+        if (sdesc) atomicAdd(cnt + kCnStartDescents, sdesc);
+    }
+}
+
+// rowptr entries clamped into [0, nnz] and made non-decreasing locally, so that later planner
+// kernels stay in bounds even before the validation result is read back.
+__device__ __forceinline__ int64_t clamp_ptr(const int32_t* rowptr, int64_t i, int64_t nnz)
+{
+    int64_t r = __ldg(rowptr + i);
+    return r < 0 ? 0 : (r > nnz ? nnz : r);
+}
+
+// ---------------------------------------------------------------------------------------------
+// residual row list when no window exists: every row, merge start = rowptr[i] + i
+// ---------------------------------------------------------------------------------------------
+__global__ void k_rl_all_rows(const int32_t* __restrict__ rowptr, int32_t m, int64_t nnz,
+                              int32_t* rl_rows, int32_t* rl_start)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < m) rl_rows[i] = (int32_t)i;
+        int64_t r = clamp_ptr(rowptr, i, nnz);
+        if (i == m) r = nnz;
+        rl_start[i] = (int32_t)(r + i);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// a8: merge-path chunk boundaries with snapping.  Boundary c sits at merge item c*W unless that
+// item falls in a residual row with 2*(len+1) <= W, in which case it moves to the row's start.
+// rl_start must be non-decreasing (guaranteed for valid inputs; clamped otherwise).
+// ---------------------------------------------------------------------------------------------
+__global__ void k_chunks(const int32_t* __restrict__ rl_start, int64_t n_rl, int64_t T, int64_t W,
+                         int64_t nc, int32_t* chunk_b, int32_t* chunk_k0)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= nc;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b;
+        if (c == 0) b = 0;
+        else if (c == nc) b = T;
+        else {
+            int64_t d = c * W;
+            int64_t k = upper_minus_one(rl_start, n_rl, d);
+            int64_t rlen = (int64_t)__ldg(rl_start + k + 1) - __ldg(rl_start + k) - 1;
+            b = (2 * (rlen + 1) <= W) ? (int64_t)__ldg(rl_start + k) : d;
+        }
+        chunk_b[c] = (int32_t)b;
+        if (c < nc) chunk_k0[c] = (int32_t)upper_minus_one(rl_start, n_rl, b);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// pieces per residual-list row and split rows.  A row is assembled from several pieces when a
+// chunk boundary cuts it or when a non-absorbing dense window also contributes to it.
+// ---------------------------------------------------------------------------------------------
+struct PieceInfo {
+    const int32_t* rl_rows;
+    const int32_t* rl_start;
+    const int32_t* chunk_b;
+    const int8_t* row_state;  // 2 = in a non-absorbing dense window; nullptr = none
+    int64_t nc;
+    __device__ __forceinline__ void pieces(int64_t k, int32_t* i_out, int32_t* np, int32_t* base) const
+    {
+        int32_t i = __ldg(rl_rows + k);
+        int64_t s = __ldg(rl_start + k), e = __ldg(rl_start + k + 1);
+        int64_t fc = upper_minus_one(chunk_b, nc, s);
+        int64_t lc = upper_minus_one(chunk_b, nc, e - 1);
+        int hd = (row_state && row_state[i] == 2) ? 1 : 0;
+        *i_out = i;
+        *np = (int32_t)(lc - fc + 1 + hd);
+        *base = (int32_t)(fc - hd);
+    }
+};
+
+// packed scan value: (is_split << 32) | (is_split ? pieces : 0)
+struct PieceLoad {
+    PieceInfo pi;
+    __device__ __forceinline__ int64_t operator()(int64_t k) const
+    {
+        int32_t i, np, base;
+        pi.pieces(k, &i, &np, &base);
+        return np >= 2 ? ((int64_t)1 << 32) | (int64_t)np : 0;
+    }
+};
+
+struct PieceStore {
+    PieceInfo pi;
+    int32_t* row_split;
+    int32_t* split_row;
+    int32_t* split_np;
+    int32_t* split_slot;
+    int32_t* split_base;
+    __device__ __forceinline__ void operator()(int64_t k, int64_t pre, int64_t v) const
+    {
+        if (v == 0) return;
+        int32_t i, np, base;
+        pi.pieces(k, &i, &np, &base);
+        int64_t s = pre >> 32;
+        row_split[i] = (int32_t)s;
+        split_row[s] = i;
+        split_np[s] = np;
+        split_slot[s] = (int32_t)(pre & 0xffffffffLL);
+        split_base[s] = base;
+    }
+};
+
+// ---------------------------------------------------------------------------------------------
+// a9: work items and their cost classes (floor log2 of the Eq. 1 cost), heaviest class first
+// ---------------------------------------------------------------------------------------------
+__global__ void k_item_costs(const int32_t* __restrict__ chunk_b, int64_t nc, int64_t group,
+                             int64_t n_dwin, const int64_t* __restrict__ dcost, int64_t n_items,
+                             int64_t cost_res, int64_t* item_cost)
+{
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n_items;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c;
+        if (it < n_dwin) c = dcost[it];
+        else {
+            int64_t q = it - n_dwin;
+            int64_t c0 = q * group, c1 = c0 + group < nc ? c0 + group : nc;
+            c = ((int64_t)__ldg(chunk_b + c1) - __ldg(chunk_b + c0)) * cost_res;
+        }
+        item_cost[it] = c;
+    }
+}
+
+__device__ __forceinline__ int cost_class(int64_t c) { return c <= 1 ? 0 : 63 - __clzll((unsigned long long)c); }
+
+struct CostKey {
+    const int64_t* cost;
+    __device__ __forceinline__ int operator()(int64_t i) const { return cost_class(cost[i]); }
+};
+struct QueueEmit {
+    int32_t* queue;
+    __device__ __forceinline__ void operator()(int64_t i, int64_t pos) const { queue[pos] = (int32_t)i; }
+};
+
+__global__ void k_bucket_offsets(int32_t* hist, int64_t nblocks)
+{
+    __shared__ int64_t tot[kSortBuckets];
+    __shared__ int64_t base[kSortBuckets];
+    const int b = threadIdx.x;
+    if (b < kSortBuckets) {
+        int64_t t = 0;
+        for (int64_t k = 0; k < nblocks; ++k) t += hist[k * kSortBuckets + b];
+        tot[b] = t;
+    }
+    __syncthreads();
+    if (b == 0) {
+        int64_t acc = 0;
+        for (int q = kSortBuckets - 1; q >= 0; --q) {
+            base[q] = acc;
+            acc += tot[q];
+        }
+    }
+    __syncthreads();
+    if (b < kSortBuckets) {
+        int64_t acc = base[b];
+        for (int64_t k = 0; k < nblocks; ++k) {
+            int32_t h = hist[k * kSortBuckets + b];
+            hist[k * kSortBuckets + b] = (int32_t)acc;
+            acc += h;
+        }
+    }
+}
+
+// fill with a 32-bit value
+__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+static unsigned grid_for(int64_t n, int threads = 256)
+{
+    int64_t g = ceil_div(n > 0 ? n : 1, threads);
+    return (unsigned)(g < 8 * 152 * 8 ? g : 8 * 152 * 8);
+}
+
+ns_status_t plan_check_tune(const ns_tune_t& t)
+{
+    if (!(t.TM == 16 || t.TM == 32 || t.TM == 64)) return NS_ERR_INVALID;
+    if (!(t.TK == 16 || t.TK == 32)) return NS_ERR_INVALID;
+    if (t.chunk_nnz < 2 || t.chunk_nnz > (1 << 20)) return NS_ERR_INVALID;
+    if (t.group != kExecWarps) return NS_ERR_INVALID;
+    if (t.cost_tc < 0 || t.cost_res < 0 || t.absorb_cap < 0) return NS_ERR_INVALID;
+    if (t.col_order != 0 && t.col_order != 1) return NS_ERR_INVALID;
+    return NS_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// orchestration
+// ---------------------------------------------------------------------------------------------
+static ns_status_t splits_and_queue(Plan* P, const WindowResult* W, cudaStream_t s, int64_t* totals)
+{
+    const int64_t m = P->st.m;
+    const int64_t n_rl = P->st.n_rl;
+    const int64_t nc = P->st.n_chunks;
+    const int64_t T = P->st.T;
+    const int64_t Wn = P->tune.chunk_nnz;
+
+    if (nc > 0) {
+        k_chunks<<<grid_for(nc + 1), 256, 0, s>>>(P->rl_start, n_rl, T, Wn, nc, P->chunk_b, P->chunk_k0);
+        NS_LAUNCH_CHECK();
+    } else {
+        NS_CUDA_TRY(cudaMemsetAsync(P->chunk_b, 0, sizeof(int32_t), s));
+    }
+    if (m > 0) {
+        k_fill_i32<<<grid_for(m), 256, 0, s>>>(P->row_split, m, -1);
+        NS_LAUNCH_CHECK();
+    }
+    Arena tmp;
+    int64_t* partial = nullptr;
+    int32_t* hist = nullptr;
+    tmp.reserve(&partial, scan_partials(n_rl));
+    tmp.reserve(&hist, bucket_hist_size(P->st.n_items));
+    NS_TRY(tmp.commit(s));
+    if (n_rl > 0 && nc > 0) {
+        PieceInfo pi{P->rl_rows, P->rl_start, P->chunk_b, W ? W->row_state : nullptr, nc};
+        PieceStore st{pi, P->row_split, P->split_row, P->split_np, P->split_slot, P->split_base};
+        NS_TRY(device_scan<int64_t>(PieceLoad{pi}, st, n_rl, partial, totals, s));
+    }
+    if (P->st.n_items > 0) {
+        k_item_costs<<<grid_for(P->st.n_items), 256, 0, s>>>(P->chunk_b, nc, P->tune.group,
+                                                              P->st.n_dwin, W ? W->dcost : nullptr,
+                                                              P->st.n_items, P->tune.cost_res,
+                                                              P->item_cost);
+        NS_LAUNCH_CHECK();
+        NS_TRY(bucket_sort_desc(CostKey{P->item_cost}, QueueEmit{P->queue}, P->st.n_items, hist, s));
+    }
+    tmp.release(s);
+    return NS_OK;
+}
+
+static ns_status_t report_invalid(const unsigned long long* hc)
+{
+    set_error("invalid CSR: %llu out-of-range columns, %llu bad row pointers, %llu "
+              "unsorted/duplicate positions",
+              hc[kCnBadRange], hc[kCnBadPtr], hc[kCnDescents] - hc[kCnStartDescents]);
+    return NS_ERR_INVALID;
+}
+
+static bool csr_ok(const unsigned long long* hc)
+{
+    return !hc[kCnBadRange] && !hc[kCnBadPtr] && hc[kCnDescents] == hc[kCnStartDescents];
+}
+
+ns_status_t plan_build(Plan* P, const ns_csr_t* A, int32_t K, ns_dtype_t dt, const ns_tune_t* tune,
+                       cudaStream_t s)
+{
+    const int64_t m = A->m, n = A->n, nnz = A->nnz;
+    P->tune = *tune;
+    P->dtype = dt;
+    P->K = K;
+    P->st.m = m;
+    P->st.n = n;
+    P->st.nnz = nnz;
+    P->st.K = K;
+    P->st.b_bf16 = dt == NS_BF16;
+    P->st.TM = tune->TM;
+    P->st.TK = tune->TK;
+
+    // ---- inputs on the device (a host CSR is copied; a device CSR is referenced) ----
+    if (A->on_device) {
+        P->rowptr = A->rowptr;
+        P->colidx = A->colidx;
+        P->vals = A->vals;
+    } else {
+        Arena in;
+        int32_t *rp = nullptr, *ci = nullptr;
+        float* v = nullptr;
+        in.reserve(&rp, m + 1);
+        in.reserve(&ci, nnz);
+        in.reserve(&v, nnz);
+        NS_TRY(in.commit(s));
+        P->blocks.push_back(in.take());
+        NS_CUDA_TRY(cudaMemcpyAsync(rp, A->rowptr, sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice, s));
+        if (nnz) {
+            NS_CUDA_TRY(cudaMemcpyAsync(ci, A->colidx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s));
+            NS_CUDA_TRY(cudaMemcpyAsync(v, A->vals, sizeof(float) * nnz, cudaMemcpyHostToDevice, s));
+        }
+        P->rowptr = rp;
+        P->colidx = ci;
+        P->vals = v;
+    }
+
+    // ---- control block ----
+    unsigned long long* counters = nullptr;  // validation counters
+    int64_t* totals = nullptr;               // [0] packed split total, [1..] window totals
+    {
+        Arena a;
+        a.reserve(&P->ctrl, 8);
+        a.reserve(&counters, 8);
+        a.reserve(&totals, 16);
+        a.reserve(&P->desc_dev, 1);
+        NS_TRY(a.commit(s));
+        P->blocks.push_back(a.take());
+        NS_CUDA_TRY(cudaMemsetAsync(P->ctrl, 0, sizeof(int32_t) * 8, s));
+        NS_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * 8, s));
+        NS_CUDA_TRY(cudaMemsetAsync(totals, 0, sizeof(int64_t) * 16, s));
+    }
+
+    // ---- a1: validation ----
+    if (nnz > 0) {
+        k_check_elems<<<grid_for(nnz), 256, 0, s>>>(P->colidx, nnz, (int32_t)n, counters);
+        NS_LAUNCH_CHECK();
+    }
+    k_check_rows<<<grid_for(m + 1), 256, 0, s>>>(P->rowptr, P->colidx, (int32_t)m, nnz, counters);
+    NS_LAUNCH_CHECK();
+
+    const bool windows_on = tune->tau_tile != kTauInf && m > 0;
+    WindowResult win{};
+    if (!windows_on) {
+        // everything is residual: the residual CSR is A itself, every row in the list
+        P->st.n_res = nnz;
+        P->st.n_rl = m;
+        P->st.T = nnz + m;
+        P->res_rowptr = P->rowptr;
+        P->res_col = P->colidx;
+        P->res_val = P->vals;
+    } else {
+        // the window kernels read row contents: validation must pass first
+        unsigned long long hc[8];
+        NS_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof hc, cudaMemcpyDeviceToHost, s));
+        NS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (!csr_ok(hc)) return report_invalid(hc);
+        NS_TRY(window_pass(P, &win, s));  // sets m_aic .. T and the residual / window arrays
+    }
+    const int64_t n_rl = P->st.n_rl;
+    const int64_t T = P->st.T;
+    const int64_t nc = T > 0 ? ceil_div(T, tune->chunk_nnz) : 0;
+    P->st.n_chunks = nc;
+    P->st.n_items = P->st.n_dwin + ceil_div(nc, tune->group);
+    {
+        Arena a;
+        if (!windows_on) {
+            a.reserve(&P->rl_rows, n_rl);
+            a.reserve(&P->rl_start, n_rl + 1);
+        }
+        a.reserve(&P->chunk_b, nc + 1);
+        a.reserve(&P->chunk_k0, nc);
+        a.reserve(&P->row_split, m);
+        a.reserve(&P->split_row, n_rl);  // split rows are residual-list rows
+        a.reserve(&P->split_np, n_rl);
+        a.reserve(&P->split_slot, n_rl);
+        a.reserve(&P->split_base, n_rl);
+        a.reserve(&P->queue, P->st.n_items);
+        a.reserve(&P->item_cost, P->st.n_items);
+        NS_TRY(a.commit(s));
+        P->blocks.push_back(a.take());
+    }
+    if (!windows_on) {
+        k_rl_all_rows<<<grid_for(m + 1), 256, 0, s>>>(P->rowptr, (int32_t)m, nnz, P->rl_rows, P->rl_start);
+        NS_LAUNCH_CHECK();
+    }
+    NS_TRY(splits_and_queue(P, windows_on ? &win : nullptr, s, totals));
+
+    // ---- one readback: validation counters and split totals ----
+    unsigned long long hc[8];
+    int64_t ht[16];
+    NS_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof hc, cudaMemcpyDeviceToHost, s));
+    NS_CUDA_TRY(cudaMemcpyAsync(ht, totals, sizeof ht, cudaMemcpyDeviceToHost, s));
+    NS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (win.temp.ptr) {
+        NS_CUDA_TRY(cudaFreeAsync(win.temp.ptr, s));
+        win.temp = DevBlock{};
+    }
+    if (!csr_ok(hc)) return report_invalid(hc);
+    P->st.n_split = ht[0] >> 32;
+    P->st.n_slots = ht[0] & 0xffffffffLL;
+
+    // ---- execution scratch, sized exactly ----
+    {
+        Arena a;
+        a.reserve(&P->slots, P->st.n_slots * (int64_t)K);
+        a.reserve(&P->split_cnt, P->st.n_split);
+        NS_TRY(a.commit(s));
+        P->blocks.push_back(a.take());
+        NS_CUDA_TRY(cudaMemsetAsync(P->split_cnt, 0, sizeof(int32_t) * (P->st.n_split > 0 ? P->st.n_split : 1), s));
+    }
+    return NS_OK;
+}
+
+}  // namespace ns

@@ -1,0 +1,54 @@
+"""The C ABI library loads and exports every entry point the header declares (CPU only);
+host-side helpers of the cost model agree with the paper's closed forms."""
+import os
+import re
+
+import pytest
+
+import oracle.formulas as F
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ns():
+    import __graft_entry__ as g
+    g._build_module().build()
+    import paper_2606_22482_gb300 as ns
+    return ns
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(ns_[a-z0-9_]+)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_symbols_exported(ns):
+    import ctypes
+    lib = ctypes.CDLL(ns._abi.LIB_PATH)
+    declared = _declared()
+    assert len(declared) >= 25
+    missing = [n for n in declared if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(ns._abi.SIGNATURES) == declared
+
+
+def test_tune_default(ns):
+    t = ns.tune_default()
+    assert (t.TM, t.TK, t.tau_tile, t.group) == (16, 16, ns.NS_TAU_INF, 4)
+
+
+def test_cost_helpers_match_closed_forms(ns):
+    for p_res, p_tc, r in [(1e9, 1e12, 1.0), (3e9, 6e12, 2.0), (5e10, 1e11, 1.0)]:
+        assert ns.lib.ns_cost_alpha(p_res, p_tc, r) == pytest.approx(F.alpha(p_res, p_tc, r), rel=1e-15)
+    for a, tm, tk in [(0.002, 16, 16), (0.1, 16, 16), (0.25, 64, 32), (1.0, 16, 16), (0.0, 16, 16)]:
+        assert ns.lib.ns_cost_tau(a, tm, tk) == F.tau_tile(a, tm, tk)
+    assert ns.lib.ns_skew(2.0, 1.0) == F.skew(2.0, 1.0)
+    assert ns.lib.ns_skew(1.0, 3.0) == F.skew(1.0, 3.0)

@@ -52,10 +52,22 @@ void Arena::release(cudaStream_t s)
     reqs.clear();
 }
 
+// Stream-ordered release: the blocks go back to the pool after everything already enqueued on
+// the stream of the last plan/execute call, so a destroy right after an asynchronous execute
+// never frees memory a running kernel still reads.
 Plan::~Plan()
 {
-    for (auto& b : blocks)
-        if (b.ptr) cudaFree(b.ptr);
+    bool failed = false;
+    for (auto& b : blocks) {
+        if (!b.ptr) continue;
+        if (!failed && cudaFreeAsync(b.ptr, last_stream) != cudaSuccess) {
+            (void)cudaGetLastError();
+            failed = true;
+            cudaDeviceSynchronize();
+        }
+        if (failed) cudaFree(b.ptr);
+        b.ptr = nullptr;
+    }
 }
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -91,7 +103,40 @@ static ns_status_t check_K(int32_t K)
     return NS_OK;
 }
 
-ns_status_t exec_launch_plan(Plan* P, cudaStream_t s);
+ns_status_t plan_create(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, const ns_tune_t* tune,
+                        cudaStream_t st, Plan** out)
+{
+    *out = nullptr;
+    NS_TRY(check_csr_args(A));
+    NS_TRY(check_K(K));
+    if (b_dtype != NS_F32 && b_dtype != NS_BF16) {
+        set_error("unknown dtype");
+        return NS_ERR_INVALID;
+    }
+    ns_tune_t t;
+    if (tune) t = *tune;
+    else ns_tune_default(&t);
+    if (plan_check_tune(t) != NS_OK) {
+        set_error("invalid tune (TM in {16,32,64}, TK in {16,32}, group=%d, chunk_nnz >= 2)", kExecWarps);
+        return NS_ERR_INVALID;
+    }
+    Plan* P = new (std::nothrow) Plan();
+    if (!P) {
+        set_error("host allocation failed");
+        return NS_ERR_OOM;
+    }
+    cudaGetDevice(&P->device);
+    P->last_stream = st;
+    ns_status_t r = plan_build(P, A, K, b_dtype, &t, st);
+    if (r != NS_OK) {
+        cudaStreamSynchronize(st);
+        (void)cudaGetLastError();
+        delete P;
+        return r;
+    }
+    *out = P;
+    return NS_OK;
+}
 
 }  // namespace ns
 
@@ -143,33 +188,8 @@ ns_status_t ns_spmm_plan(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, const
         return NS_ERR_INVALID;
     }
     *out = nullptr;
-    NS_TRY(check_csr_args(A));
-    NS_TRY(check_K(K));
-    if (b_dtype != NS_F32 && b_dtype != NS_BF16) {
-        set_error("unknown dtype");
-        return NS_ERR_INVALID;
-    }
-    ns_tune_t t;
-    if (tune) t = *tune;
-    else ns_tune_default(&t);
-    if (plan_check_tune(t) != NS_OK) {
-        set_error("invalid tune (TM in {16,32,64}, TK in {16,32}, group=%d, chunk_nnz >= 2)", kExecWarps);
-        return NS_ERR_INVALID;
-    }
-    Plan* P = new (std::nothrow) Plan();
-    if (!P) {
-        set_error("host allocation failed");
-        return NS_ERR_OOM;
-    }
-    cudaGetDevice(&P->device);
-    cudaStream_t st = static_cast<cudaStream_t>(s);
-    ns_status_t r = plan_build(P, A, K, b_dtype, &t, st);
-    if (r != NS_OK) {
-        cudaStreamSynchronize(st);
-        (void)cudaGetLastError();
-        delete P;
-        return r;
-    }
+    Plan* P = nullptr;
+    NS_TRY(plan_create(A, K, b_dtype, tune, static_cast<cudaStream_t>(s), &P));
     *out = reinterpret_cast<ns_plan_t>(P);
     return NS_OK;
 }
@@ -195,6 +215,15 @@ ns_status_t ns_spmm_execute(ns_plan_t p, const void* B, int64_t ldb, float* C, i
         return NS_ERR_UNSUPPORTED;
     }
     cudaStream_t st = static_cast<cudaStream_t>(s);
+    if (st != P->last_stream) {
+        // later frees are ordered on the new stream; make it wait for the old one first
+        cudaEvent_t ev;
+        NS_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaEventRecord(ev, P->last_stream);
+        cudaStreamWaitEvent(st, ev, 0);
+        cudaEventDestroy(ev);
+        P->last_stream = st;
+    }
     // a device status word left by an earlier launch of this plan
     if (P->desc_valid) {
         int32_t status = 0;
@@ -206,7 +235,8 @@ ns_status_t ns_spmm_execute(ns_plan_t p, const void* B, int64_t ldb, float* C, i
             return NS_ERR_TIMEOUT;
         }
         if (status) {
-            set_error("an earlier launch reported internal status %d", status);
+            set_error("an earlier launch found an out-of-range plan index (status %d); results of "
+                      "that launch are invalid", status);
             return NS_ERR_CUDA;
         }
     }
@@ -248,7 +278,7 @@ static bool find_array(Plan* P, const char* name, ArrayRef* a)
     }
     A(aic_rows, P->aic_rows, s.m_aic, 4)
     A(win_rows, P->win_rows, s.n_win * TM, 4)
-    A(win_dptr, P->win_dptr, s.n_win > 0 ? s.n_win + 1 : 1, 4)
+    A(win_dptr, P->win_dptr, s.n_win + 1, 4)
     A(dwin, P->dwin, s.n_dwin, 4)
     A(dwin_absorb, P->dwin_absorb, s.n_dwin, 4)
     A(dtile_cols, P->dtile_cols, s.n_dtiles * TK, 4)
@@ -285,8 +315,8 @@ ns_status_t ns_plan_array_info(ns_plan_t p, const char* name, int64_t* count, in
         set_error("unknown plan array '%s'", name);
         return NS_ERR_NOT_FOUND;
     }
-    // arrays that do not exist in this plan (no windows) have zero length
-    *count = a.ptr ? a.count : 0;
+    // arrays a plan does not materialise (no windows) export as zeros of the reference length
+    *count = a.count;
     *esize = a.esize;
     return NS_OK;
 }
@@ -303,11 +333,15 @@ ns_status_t ns_plan_export(ns_plan_t p, const char* name, void* host_dst, int64_
         set_error("unknown plan array '%s'", name);
         return NS_ERR_NOT_FOUND;
     }
-    int64_t need = a.ptr ? a.count * a.esize : 0;
+    int64_t need = a.count * a.esize;
     if (need == 0) return NS_OK;
     if (!host_dst || bytes < need) {
         set_error("destination too small: need %lld bytes", (long long)need);
         return NS_ERR_INVALID;
+    }
+    if (!a.ptr) {
+        memset(host_dst, 0, (size_t)need);
+        return NS_OK;
     }
     NS_CUDA_TRY(cudaMemcpy(host_dst, a.ptr, (size_t)need, cudaMemcpyDeviceToHost));
     return NS_OK;

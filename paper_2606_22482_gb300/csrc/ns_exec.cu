@@ -17,7 +17,6 @@
 // L2 policy (Section 6.2.1 hot-B staging in GPU form): A's arrays and C are streamed with an
 // evict-first policy, B rows are loaded with evict-last so that reused B rows stay in L2.
 #include "ns_internal.cuh"
-#include "ns_dense.cuh"
 
 namespace ns {
 
@@ -187,6 +186,11 @@ __device__ __forceinline__ void gather_accumulate(const ExecDesc& D, int64_t z0,
         if (lane < cnt) {
             mc = ld_stream_i32<HINT>(D.res_col + zb + lane, pol.first);
             mv = ld_stream_f32<HINT>(D.res_val + zb + lane, pol.first);
+            if ((unsigned)mc >= (unsigned)D.n) {  // guard: never gather outside B
+                atomicOr(D.status, kStatusInternal);
+                mc = 0;
+                mv = 0.f;
+            }
         }
         // 4 independent B rows in flight per lane
         for (int j0 = 0; j0 < cnt; j0 += 4 * G) {
@@ -239,10 +243,19 @@ __device__ void residual_chunk(const ExecDesc& D, int32_t c, int lane, const Pol
     int64_t k = __ldg(D.chunk_k0 + c);
     int64_t x = b0;
     while (x < b1) {
+        // guards: a corrupt plan sets the status word and stops instead of faulting
+        if (k < 0 || k >= D.n_rl) {
+            if (lane == 0) atomicOr(D.status, kStatusInternal);
+            return;
+        }
         const int32_t i = __ldg(D.rl_rows + k);
         const int64_t s = __ldg(D.rl_start + k), e = __ldg(D.rl_start + k + 1);
-        const int64_t zrow = __ldg(D.res_rowptr + i);
+        const int64_t zrow = (i >= 0 && i < D.m) ? __ldg(D.res_rowptr + i) : -1;
         const int64_t xe = b1 < e - 1 ? b1 : e - 1;  // nonzero merge items of this row in chunk
+        if (zrow < 0 || x < s || e <= s || zrow + (xe - s) > D.n_res) {
+            if (lane == 0) atomicOr(D.status, kStatusInternal);
+            return;
+        }
         float4 acc[VPL];
 #pragma unroll
         for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -257,6 +270,12 @@ __device__ void residual_chunk(const ExecDesc& D, int32_t c, int lane, const Pol
         }
     }
 }
+
+}  // namespace ns
+
+#include "ns_dense.cuh"
+
+namespace ns {
 
 // ---------------------------------------------------------------------------------------------
 // the persistent kernel
@@ -282,7 +301,7 @@ __global__ void __launch_bounds__(kExecThreads) k_exec(const ExecDesc* __restric
         const int32_t di = queue_desc ? __ldg(queue_desc + t) : 0;
         const ExecDesc& D = descs[di];
         if (DENSE && it < D.n_dwin) {
-            dense_item<BF16, HINT>(D, it, smem_raw, pol.first, pol.last);
+            dense_item<L, VPL, BF16, HINT>(D, it, smem_raw, pol);
         } else {
             const int32_t c = (it - D.n_dwin) * D.group + warp;
             if (c < D.n_chunks) residual_chunk<L, VPL, BF16, HINT>(D, c, lane, pol);
@@ -339,6 +358,10 @@ void fill_desc(const Plan* P, const void* B, int64_t ldb, float* C, int64_t ldc,
     d->group = P->tune.group;
     d->l2_hints = P->tune.l2_hints;
     d->m = (int32_t)P->st.m;
+    d->n = (int32_t)P->st.n;
+    d->n_rl = (int32_t)P->st.n_rl;
+    d->n_res = (int32_t)P->st.n_res;
+    d->status = P->ctrl + 2;
 }
 
 typedef void (*ExecKernel)(const ExecDesc*, const int32_t*, const int32_t*, int64_t, int32_t*);
@@ -379,28 +402,49 @@ int num_sms(int device)
     return cached[device];
 }
 
-ns_status_t exec_launch_plan(Plan* P, cudaStream_t s)
+// Kernel attributes and the persistent grid (resident CTAs on every SM, at most n_items).
+// Must run outside stream capture.
+ns_status_t exec_prepare(int64_t n_items, int K, int TM, int TK, bool bf16, bool hint, bool dense,
+                         int* grid_out)
 {
-    const bool dense = P->st.n_dwin > 0;
-    const bool bf16 = P->dtype == NS_BF16;
-    const bool hint = P->tune.l2_hints != 0;
-    ExecKernel kern = select_kernel(P->K, bf16, hint, dense);
-    const size_t smem = dense ? dense_smem_bytes(P->K, P->tune.TM, P->tune.TK, bf16) : 0;
+    ExecKernel kern = select_kernel(K, bf16, hint, dense);
+    const size_t smem = dense ? dense_smem_bytes(K, TM, TK, bf16) : 0;
     if (dense) NS_TRY(dense_prepare(reinterpret_cast<const void*>(kern), smem));
-    if (P->exec_grid == 0) {
-        int per_sm = 0;
-        NS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kExecThreads, smem));
-        if (per_sm < 1) per_sm = 1;
-        int dev = 0;
-        NS_CUDA_TRY(cudaGetDevice(&dev));
-        int64_t g = (int64_t)per_sm * num_sms(dev);
-        if (g > P->st.n_items) g = P->st.n_items;
-        P->exec_grid = (int)(g > 0 ? g : 1);
-    }
-    if (P->st.n_items == 0) return NS_OK;
-    kern<<<P->exec_grid, kExecThreads, smem, s>>>(P->desc_dev, P->queue, nullptr, P->st.n_items, P->ctrl);
+    int per_sm = 0;
+    NS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kExecThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int dev = 0;
+    NS_CUDA_TRY(cudaGetDevice(&dev));
+    int64_t g = (int64_t)per_sm * num_sms(dev);
+    if (g > n_items) g = n_items;
+    *grid_out = (int)(g > 0 ? g : 1);
+    return NS_OK;
+}
+
+// One persistent launch over `n_items` work items.  queue[t] is an item id of descriptor
+// queue_desc[t] (descriptor 0 when queue_desc is NULL).  All descriptors share K, dtype and L2
+// policy; `dense` selects the kernel with the tensor-core item compiled in.  *grid_cache keeps
+// the occupancy-derived grid between launches (0 = compute).
+ns_status_t exec_launch(const ExecDesc* descs, const int32_t* queue, const int32_t* queue_desc,
+                        int64_t n_items, int32_t* ctrl, int K, int TM, int TK, bool bf16, bool hint,
+                        bool dense, int* grid_cache, cudaStream_t s)
+{
+    ExecKernel kern = select_kernel(K, bf16, hint, dense);
+    const size_t smem = dense ? dense_smem_bytes(K, TM, TK, bf16) : 0;
+    int grid = grid_cache ? *grid_cache : 0;
+    if (grid == 0) NS_TRY(exec_prepare(n_items, K, TM, TK, bf16, hint, dense, &grid));
+    if (grid_cache) *grid_cache = grid;
+    if (n_items == 0) return NS_OK;
+    kern<<<grid, kExecThreads, smem, s>>>(descs, queue, queue_desc, n_items, ctrl);
     NS_LAUNCH_CHECK();
     return NS_OK;
+}
+
+ns_status_t exec_launch_plan(Plan* P, cudaStream_t s)
+{
+    return exec_launch(P->desc_dev, P->queue, nullptr, P->st.n_items, P->ctrl, P->K, P->tune.TM,
+                       P->tune.TK, P->dtype == NS_BF16, P->tune.l2_hints != 0, P->st.n_dwin > 0,
+                       &P->exec_grid, s);
 }
 
 }  // namespace ns

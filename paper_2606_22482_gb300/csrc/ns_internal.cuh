@@ -125,7 +125,9 @@ struct ExecDesc {
     float* C;
     int64_t ldb, ldc;
     int32_t K, b_bf16, TM, TK, group, l2_hints;
-    int32_t m, pad_;
+    int32_t m, n;          // shape of A (bounds guards)
+    int32_t n_rl, n_res;   // residual list rows, residual nonzeros (bounds guards)
+    int32_t* status;       // device status word (kStatus* bits)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -179,6 +181,7 @@ struct Plan {
     bool desc_valid = false;
     std::vector<DevBlock> blocks;  // every device allocation the plan owns
     int exec_grid = 0;
+    cudaStream_t last_stream = nullptr;  // stream of the last plan/execute call: frees go there
     ~Plan();
 };
 
@@ -204,5 +207,13 @@ ns_status_t plan_check_tune(const ns_tune_t& t);
 
 // execute entry (ns_exec.cu)
 void fill_desc(const Plan* P, const void* B, int64_t ldb, float* C, int64_t ldc, ExecDesc* d);
+ns_status_t exec_launch(const ExecDesc* descs, const int32_t* queue, const int32_t* queue_desc,
+                        int64_t n_items, int32_t* ctrl, int K, int TM, int TK, bool bf16, bool hint,
+                        bool dense, int* grid_cache, cudaStream_t s);
+ns_status_t exec_launch_plan(Plan* P, cudaStream_t s);
+ns_status_t exec_prepare(int64_t n_items, int K, int TM, int TK, bool bf16, bool hint, bool dense,
+                         int* grid_out);
+ns_status_t plan_create(const ns_csr_t* A, int32_t K, ns_dtype_t dt, const ns_tune_t* tune,
+                        cudaStream_t s, Plan** out);  // checks + build; on error nothing is kept
 
 }  // namespace ns

@@ -5,31 +5,6 @@
 using namespace ns;
 
 extern "C" {
-ns_status_t ns_batch_plan(const ns_csr_t*, int32_t, const int32_t*, ns_dtype_t, const ns_tune_t*,
-                          ns_stream_t, ns_batch_t* out)
-{
-    if (out) *out = nullptr;
-    set_error("batched form not built yet");
-    return NS_ERR_UNSUPPORTED;
-}
-ns_status_t ns_batch_execute(ns_batch_t, const void* const*, float* const*, ns_stream_t)
-{
-    set_error("batched form not built yet");
-    return NS_ERR_UNSUPPORTED;
-}
-ns_status_t ns_batch_stats(ns_batch_t, int64_t*, int64_t*)
-{
-    set_error("batched form not built yet");
-    return NS_ERR_UNSUPPORTED;
-}
-ns_status_t ns_batch_destroy(ns_batch_t) { return NS_OK; }
-ns_status_t ns_autotune(const ns_csr_t*, int32_t, ns_dtype_t, ns_stream_t, ns_tune_t* out,
-                        ns_tune_report_t*)
-{
-    if (out) ns_tune_default(out);
-    set_error("autotuner not built yet");
-    return NS_ERR_UNSUPPORTED;
-}
 ns_status_t ns_serve_create(const ns_serve_cfg_t*, ns_server_t* out)
 {
     if (out) *out = nullptr;

@@ -379,6 +379,10 @@ ns_status_t plan_build(Plan* P, const ns_csr_t* A, int32_t K, ns_dtype_t dt, con
     NS_LAUNCH_CHECK();
 
     const bool windows_on = tune->tau_tile != kTauInf && m > 0;
+    if (tune->tau_tile != kTauInf && (int64_t)tune->TM * K > 16384) {
+        set_error("dense tiles need TM * K <= 16384 (TM=%d, K=%d); lower TM", tune->TM, K);
+        return NS_ERR_UNSUPPORTED;
+    }
     WindowResult win{};
     if (!windows_on) {
         // everything is residual: the residual CSR is A itself, every row in the list

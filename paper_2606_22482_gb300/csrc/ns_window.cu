@@ -1,13 +1,784 @@
-// ns_window.cu -- the window pass of the planner (row/column extraction, windows, compaction,
-// density binning, residual CSR).
+// ns_window.cu -- the window pass of the device planner (arXiv 2606.22482 Sections 5.2.2, 6.1).
+//
+//   W1  row extraction (Eq. 4-5, integer threshold): rows with Len > tau_row are kept
+//   W2  column extraction inside the kept rows: columns with count <= tau_col leave
+//   W3  windows = TM consecutive kept rows; window element ranges by a scan of kept lengths
+//   W4  gather every window's kept columns (rows' sorted segments, concatenated)
+//   W5  per window (one CTA): merge the sorted row segments, run-length encode to the unique
+//       columns with counts (column compaction, Section 6.1), order them canonically (count
+//       descending then column, or column ascending), cut TK-wide tiles, bin them by density
+//       (nnz >= tau_tile), map every element to its compacted position, count dense elements
+//       per row
+//   W6  scans: dense tiles / values per window, residual row pointers, dense windows
+//   W7  dense windows: absorb decision, Eq. 1 cost, row ownership
+//   W8  residual row list with merge starts
+//   W9  emit dense tiles (columns, bitmap, packed values in bitmap order, BF16 RNE if asked)
+//   W10 residual CSR: every element outside a dense tile, original rows and column order
+// All of it is integer work with fixed orders, matching the CPU reference partition exactly.
 #include "ns_internal.cuh"
+#include "ns_scan.cuh"
+
+#include <cuda_bf16.h>
 
 namespace ns {
 
+constexpr int kWinThreads = 256;
+constexpr int kWinSmemKeys = 4096;  // windows up to this many elements sort in shared memory
+constexpr int kMaxTM = 64;
+
+// ---------------------------------------------------------------------------------------------
+// W1: kept rows
+// ---------------------------------------------------------------------------------------------
+struct KeepLoad {
+    const int32_t* rowptr;
+    int32_t tau_row;
+    __device__ __forceinline__ int64_t operator()(int64_t i) const
+    {
+        return (__ldg(rowptr + i + 1) - __ldg(rowptr + i)) > tau_row ? 1 : 0;
+    }
+};
+struct KeepStore {
+    int32_t* aic_rows;
+    __device__ __forceinline__ void operator()(int64_t i, int64_t pre, int64_t v) const
+    {
+        if (v) aic_rows[pre] = (int32_t)i;
+    }
+};
+
+// W2: column counts over kept rows (warp per kept row)
+__global__ void k_colcount(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                           const int32_t* __restrict__ aic_rows, int64_t m_aic, int32_t* colcount)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < m_aic;
+         k += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int32_t i = __ldg(aic_rows + k);
+        for (int64_t p = __ldg(rowptr + i) + lane; p < __ldg(rowptr + i + 1); p += 32)
+            atomicAdd(colcount + __ldg(colidx + p), 1);
+    }
+}
+
+// W3: kept length of kept row k (all of it when no column extraction)
+struct KeptLenLoad {
+    const int32_t* rowptr;
+    const int32_t* colidx;
+    const int32_t* aic_rows;
+    const int32_t* colcount;  // nullptr: keep every column
+    int32_t tau_col;
+    __device__ __forceinline__ int64_t operator()(int64_t k) const
+    {
+        int32_t i = __ldg(aic_rows + k);
+        int64_t b = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
+        if (!colcount) return e - b;
+        int64_t c = 0;
+        for (int64_t p = b; p < e; ++p) c += __ldg(colcount + __ldg(colidx + p)) > tau_col;
+        return c;
+    }
+};
+struct KeptLenStore {
+    int64_t* row_kbase;
+    __device__ __forceinline__ void operator()(int64_t k, int64_t pre, int64_t) const { row_kbase[k] = pre; }
+};
+
+// W4: gather kept columns and their original indices (warp per kept row)
+__global__ void k_gather_window_elems(const int32_t* __restrict__ rowptr,
+                                      const int32_t* __restrict__ colidx,
+                                      const int32_t* __restrict__ aic_rows, int64_t m_aic,
+                                      const int64_t* __restrict__ row_kbase,
+                                      const int32_t* __restrict__ colcount, int32_t tau_col,
+                                      int32_t* ekey, int32_t* eidx)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < m_aic;
+         k += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int32_t i = __ldg(aic_rows + k);
+        int64_t b = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
+        int64_t out = row_kbase[k];
+        for (int64_t p0 = b; p0 < e; p0 += 32) {
+            int64_t p = p0 + lane;
+            int32_t c = p < e ? __ldg(colidx + p) : 0;
+            bool keep = p < e && (!colcount || __ldg(colcount + c) > tau_col);
+            unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                int64_t o = out + __popc(bal & ((1u << lane) - 1u));
+                ekey[o] = c;
+                eidx[o] = (int32_t)p;
+            }
+            out += __popc(bal);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// W5: per-window compaction (one CTA per window)
+// ---------------------------------------------------------------------------------------------
+// stable merge path: elements taken from A among the first d outputs (ties go to A)
+__device__ __forceinline__ int64_t merge_corank(const int32_t* A, int64_t na, const int32_t* B,
+                                                int64_t nb, int64_t d)
+{
+    int64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+    while (lo < hi) {
+        int64_t i = (lo + hi) >> 1;
+        if (A[i] <= B[d - i - 1]) lo = i + 1;
+        else hi = i;
+    }
+    return lo;
+}
+
+// sort N keys made of R sorted runs (boundaries rb[0..R]) by pairwise merge rounds.
+// Returns the buffer holding the result (in or tmp).  rb is modified (shared memory).
+__device__ int32_t* cta_merge_runs(int32_t* in, int32_t* tmp, int64_t N, int64_t* rb, int R)
+{
+    int32_t* src = in;
+    int32_t* dst = tmp;
+    const int nt = blockDim.x;
+    while (R > 1) {
+        const int64_t S = (N + nt - 1) / nt;
+        int64_t o0 = (int64_t)threadIdx.x * S;
+        const int64_t o1 = o0 + S < N ? o0 + S : N;
+        while (o0 < o1) {
+            // pair j containing o0: largest j with rb[2j] <= o0
+            int j = 0;
+            for (int q = 0; 2 * q < R; ++q)
+                if (rb[2 * q] <= o0) j = q;
+            const int64_t ps = rb[2 * j];
+            const int64_t mid = rb[2 * j + 1 < R ? 2 * j + 1 : R];
+            const int64_t pe = rb[2 * j + 2 < R ? 2 * j + 2 : R];
+            const int64_t seg_end = o1 < pe ? o1 : pe;
+            const int32_t* A = src + ps;
+            const int32_t* B = src + mid;
+            const int64_t na = mid - ps, nb = pe - mid;
+            int64_t d = o0 - ps;
+            int64_t ia = merge_corank(A, na, B, nb, d);
+            int64_t ib = d - ia;
+            for (int64_t o = o0; o < seg_end; ++o) {
+                bool take_a = ib >= nb || (ia < na && A[ia] <= B[ib]);
+                dst[o] = take_a ? A[ia++] : B[ib++];
+            }
+            o0 = seg_end;
+        }
+        __syncthreads();
+        // next round's runs: every other boundary
+        int64_t nrb[kMaxTM / 2 + 2];
+        int nR = (R + 1) / 2;
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < nR; ++q) nrb[q] = rb[2 * q];
+            nrb[nR] = rb[R];
+            for (int q = 0; q <= nR; ++q) rb[q] = nrb[q];
+        }
+        __syncthreads();
+        R = nR;
+        int32_t* t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
+struct WinArgs {
+    // inputs
+    const int32_t* rowptr;
+    const int32_t* aic_rows;
+    const int64_t* row_kbase;  // m_aic + 1
+    const int32_t* ekey;
+    int64_t m_aic;
+    int32_t TM, TK, tau_tile, col_order;
+    // temporaries in window-element space (offset wbase)
+    int32_t* sortbuf0;
+    int32_t* sortbuf1;
+    int32_t* uasc;
+    int32_t* ucnt;  // counts of uasc entries
+    int32_t* upos;  // canonical position of uasc entries
+    int32_t* ucan;  // column at canonical position
+    int32_t* ccnt;  // count at canonical position
+    int32_t* trank; // dense rank of tile t (or -1)
+    int32_t* tvoff; // value offset of dense tile t inside the window
+    int32_t* epos;  // canonical position of each element
+    // per-window outputs
+    int32_t* win_U;
+    int32_t* win_ndt;
+    int32_t* win_ndv;
+    int64_t* win_res;   // residual nonzeros of the window's rows
+    int32_t* res_len;   // per row (m)
+};
+
+// row slot of window element e: the largest r < nrows with rb[r] <= e (empty rows share their
+// start with the next row, so the largest such r is the row that holds e)
+__device__ __forceinline__ int row_slot_of(const int64_t* rb, int nrows, int64_t e)
+{
+    int lo = 0, hi = nrows;  // answer in [lo, hi)
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (rb[mid] <= e) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
+{
+    __shared__ int64_t rb[kMaxTM + 1];   // run boundaries (relative to wbase)
+    __shared__ int64_t rb0[kMaxTM + 1];  // original row boundaries
+    __shared__ int32_t skeys[2][kWinSmemKeys];
+    __shared__ int64_t sscan[kWinThreads / 32 + 1];
+    __shared__ int32_t wc[kWinThreads / 32][kMaxTM + 1];
+    __shared__ int32_t binoff[kMaxTM + 1];
+    __shared__ int32_t dcnt[kMaxTM];
+    __shared__ int64_t s_carry[2];
+
+    const int w = blockIdx.x;
+    const int TM = a.TM, TK = a.TK;
+    const int64_t r0 = (int64_t)w * TM;
+    const int nrows = (int)(a.m_aic - r0 < TM ? a.m_aic - r0 : TM);
+    const int64_t wbase = a.row_kbase[r0];
+    const int64_t N = a.row_kbase[r0 + nrows] - wbase;
+    for (int q = threadIdx.x; q <= nrows; q += blockDim.x) {
+        rb[q] = a.row_kbase[r0 + q] - wbase;
+        rb0[q] = rb[q];
+    }
+    for (int q = threadIdx.x; q < TM; q += blockDim.x) dcnt[q] = 0;
+    __syncthreads();
+
+    // ---- sort the window's columns (merge of sorted row segments) ----
+    const bool in_smem = N <= kWinSmemKeys;
+    int32_t* b0 = in_smem ? skeys[0] : a.sortbuf0 + wbase;
+    int32_t* b1 = in_smem ? skeys[1] : a.sortbuf1 + wbase;
+    for (int64_t e = threadIdx.x; e < N; e += blockDim.x) b0[e] = a.ekey[wbase + e];
+    __syncthreads();
+    const int32_t* sorted = cta_merge_runs(b0, b1, N, rb, nrows);
+
+    // ---- run-length encode: ascending unique columns; start positions in upos (temp) ----
+    int32_t* uasc = a.uasc + wbase;
+    int32_t* ucnt = a.ucnt + wbase;
+    int32_t* upos = a.upos + wbase;
+    if (threadIdx.x == 0) s_carry[0] = 0;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < N; c0 += blockDim.x) {
+        int64_t e = c0 + threadIdx.x;
+        int64_t f = (e < N && (e == 0 || sorted[e] != sorted[e - 1])) ? 1 : 0;
+        int64_t tot;
+        int64_t pre = block_excl_scan<int64_t, kWinThreads>(f, &tot, sscan) + s_carry[0];
+        if (f) {
+            uasc[pre] = sorted[e];
+            upos[pre] = (int32_t)e;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry[0] += tot;
+        __syncthreads();
+    }
+    const int64_t U = s_carry[0];
+    for (int64_t u = threadIdx.x; u < U; u += blockDim.x) {
+        int64_t nxt = u + 1 < U ? upos[u + 1] : N;
+        ucnt[u] = (int32_t)(nxt - upos[u]);
+    }
+    __syncthreads();
+
+    // ---- canonical order ----
+    int32_t* ucan = a.ucan + wbase;
+    int32_t* ccnt = a.ccnt + wbase;
+    if (a.col_order == 1) {
+        for (int64_t u = threadIdx.x; u < U; u += blockDim.x) {
+            upos[u] = (int32_t)u;
+            ucan[u] = uasc[u];
+            ccnt[u] = ucnt[u];
+        }
+    } else {
+        // stable counting sort by count, descending (counts are 1..TM)
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (threadIdx.x <= TM) binoff[threadIdx.x] = 0;
+        __syncthreads();
+        for (int64_t u = threadIdx.x; u < U; u += blockDim.x) atomicAdd(&binoff[ucnt[u]], 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t acc = 0;
+            for (int c = TM; c >= 0; --c) {
+                int32_t h = binoff[c];
+                binoff[c] = acc;
+                acc += h;
+            }
+        }
+        __syncthreads();
+        for (int64_t c0 = 0; c0 < U; c0 += blockDim.x) {
+            for (int q = threadIdx.x; q < (kWinThreads / 32) * (kMaxTM + 1); q += blockDim.x)
+                (&wc[0][0])[q] = 0;
+            __syncthreads();
+            int64_t u = c0 + threadIdx.x;
+            int c = u < U ? ucnt[u] : -1;
+            unsigned peers = __match_any_sync(0xffffffffu, c);
+            int rk = __popc(peers & ((1u << lane) - 1u));
+            if (c >= 0 && rk == 0) wc[warp][c] = __popc(peers);
+            __syncthreads();
+            if (c >= 0) {
+                int before = 0;
+                for (int q = 0; q < warp; ++q) before += wc[q][c];
+                int32_t dest = binoff[c] + before + rk;
+                upos[u] = dest;
+                ucan[dest] = uasc[u];
+                ccnt[dest] = c;
+            }
+            __syncthreads();
+            if (threadIdx.x <= TM) {
+                int add = 0;
+                for (int q = 0; q < kWinThreads / 32; ++q) add += wc[q][threadIdx.x];
+                binoff[threadIdx.x] += add;
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+
+    // ---- tiles: nnz, density, dense rank and value offset inside the window ----
+    const int64_t ntile = (U + TK - 1) / TK;
+    int32_t* trank = a.trank + wbase;
+    int32_t* tvoff = a.tvoff + wbase;
+    if (threadIdx.x == 0) s_carry[0] = s_carry[1] = 0;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < ntile; c0 += blockDim.x) {
+        int64_t t = c0 + threadIdx.x;
+        int64_t v = 0;
+        int32_t tn = 0;
+        if (t < ntile) {
+            for (int64_t p = t * TK; p < (t + 1) * TK && p < U; ++p) tn += ccnt[p];
+            if (tn >= a.tau_tile) v = ((int64_t)1 << 32) | (int64_t)(((tn + 7) / 8) * 8);
+        }
+        int64_t tot;
+        int64_t pre = block_excl_scan<int64_t, kWinThreads>(v, &tot, sscan);
+        if (t < ntile) {
+            trank[t] = v ? (int32_t)(s_carry[0] + (pre >> 32)) : -1;
+            tvoff[t] = (int32_t)(s_carry[1] + (pre & 0xffffffffLL));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_carry[0] += tot >> 32;
+            s_carry[1] += tot & 0xffffffffLL;
+        }
+        __syncthreads();
+    }
+
+    // ---- elements: compacted position, dense counts per row ----
+    int32_t* epos = a.epos + wbase;
+    for (int64_t e = threadIdx.x; e < N; e += blockDim.x) {
+        const int32_t col = a.ekey[wbase + e];
+        int64_t lo = 0, hi = U;  // lower bound of col in uasc
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (uasc[mid] < col) lo = mid + 1;
+            else hi = mid;
+        }
+        const int32_t pos = upos[lo];
+        epos[e] = pos;
+        if (trank[pos / TK] >= 0) atomicAdd(&dcnt[row_slot_of(rb0, nrows, e)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.win_U[w] = (int32_t)U;
+        a.win_ndt[w] = (int32_t)s_carry[0];
+        a.win_ndv[w] = (int32_t)s_carry[1];
+    }
+    if (threadIdx.x < 32) {
+        int64_t rs = 0;
+        for (int r = threadIdx.x; r < nrows; r += 32) {
+            int32_t i = __ldg(a.aic_rows + r0 + r);
+            int32_t len = __ldg(a.rowptr + i + 1) - __ldg(a.rowptr + i);
+            int32_t rl = len - dcnt[r];
+            a.res_len[i] = rl;
+            rs += rl;
+        }
+        rs = warp_sum(rs);
+        if (threadIdx.x == 0) a.win_res[w] = rs;
+    }
+}
+
+// non-kept rows: the whole row is residual
+__global__ void k_res_len_free_rows(const int32_t* __restrict__ rowptr, int64_t m, int32_t tau_row,
+                                    int32_t* res_len)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t len = __ldg(rowptr + i + 1) - __ldg(rowptr + i);
+        if (len <= tau_row) res_len[i] = len;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// W6/W7: scans over windows and rows, dense windows and ownership
+// ---------------------------------------------------------------------------------------------
+struct I32Load {
+    const int32_t* p;
+    __device__ __forceinline__ int64_t operator()(int64_t i) const { return p[i]; }
+};
+struct PtrStore32 {  // out[i] = prefix (int32)
+    int32_t* out;
+    __device__ __forceinline__ void operator()(int64_t i, int64_t pre, int64_t) const { out[i] = (int32_t)pre; }
+};
+struct PtrStore64 {
+    int64_t* out;
+    __device__ __forceinline__ void operator()(int64_t i, int64_t pre, int64_t) const { out[i] = pre; }
+};
+struct DenseWinLoad {
+    const int32_t* win_ndt;
+    __device__ __forceinline__ int64_t operator()(int64_t w) const { return win_ndt[w] > 0 ? 1 : 0; }
+};
+struct DenseWinStore {
+    int32_t* dwin;
+    __device__ __forceinline__ void operator()(int64_t w, int64_t pre, int64_t v) const
+    {
+        if (v) dwin[pre] = (int32_t)w;
+    }
+};
+
+__global__ void k_dense_windows(const int32_t* __restrict__ dwin, int64_t n_dwin,
+                                const int32_t* __restrict__ win_ndt,
+                                const int64_t* __restrict__ win_res,
+                                const int32_t* __restrict__ aic_rows, int64_t m_aic, int32_t TM,
+                                int32_t TK, int32_t absorb_cap, int64_t cost_tc, int64_t cost_res,
+                                int32_t* dwin_absorb, int64_t* dcost, int8_t* row_state)
+{
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < n_dwin;
+         d += (int64_t)gridDim.x * blockDim.x) {
+        int32_t w = dwin[d];
+        int64_t r0 = (int64_t)w * TM;
+        int64_t nvalid = m_aic - r0 < TM ? m_aic - r0 : TM;
+        int64_t res = win_res[w];
+        int absorb = res <= absorb_cap;
+        dwin_absorb[d] = absorb;
+        dcost[d] = (int64_t)win_ndt[w] * TM * TK * cost_tc + ((absorb ? res : 0) + nvalid) * cost_res;
+        for (int64_t r = 0; r < nvalid; ++r) row_state[aic_rows[r0 + r]] = absorb ? 1 : 2;
+    }
+}
+
+// W8: residual list rows: free rows, and rows of non-absorbing dense windows with residual
+struct RlLoad {
+    const int8_t* row_state;
+    const int32_t* res_len;
+    __device__ __forceinline__ int64_t operator()(int64_t i) const
+    {
+        int8_t st = row_state[i];
+        int32_t rl = res_len[i];
+        bool in = st == 0 || (st == 2 && rl > 0);
+        return in ? (((int64_t)1 << 32) | (int64_t)(rl + 1)) : 0;
+    }
+};
+struct RlStore {
+    int32_t* rl_rows;
+    int32_t* rl_start;
+    __device__ __forceinline__ void operator()(int64_t i, int64_t pre, int64_t v) const
+    {
+        if (!v) return;
+        int64_t k = pre >> 32;
+        rl_rows[k] = (int32_t)i;
+        rl_start[k] = (int32_t)(pre & 0xffffffffLL);
+    }
+};
+
+// ---------------------------------------------------------------------------------------------
+// W9: emit dense tiles (one CTA per window)
+// ---------------------------------------------------------------------------------------------
+struct EmitArgs {
+    const int64_t* row_kbase;
+    const int32_t* eidx;
+    const int32_t* epos;
+    const int32_t* ucan;
+    const int32_t* trank;
+    const int32_t* tvoff;
+    const int32_t* win_U;
+    const int32_t* win_ndt;
+    const int32_t* win_dptr;
+    const int64_t* win_vbase;
+    const float* vals;
+    int64_t m_aic;
+    int32_t TM, TK, bf16;
+    int32_t* dtile_cols;
+    uint32_t* dtile_bits;
+    int32_t* dtile_voff;
+    void* dtile_vals;
+    uint8_t* pdense;  // per original element: 1 if in a dense tile
+};
+
+__global__ void __launch_bounds__(kWinThreads) k_emit_tiles(EmitArgs a)
+{
+    __shared__ int64_t rb0[kMaxTM + 1];
+    const int w = blockIdx.x;
+    if (a.win_ndt[w] == 0) return;
+    const int TM = a.TM, TK = a.TK, BW = TM * TK / 32;
+    const int64_t r0 = (int64_t)w * TM;
+    const int nrows = (int)(a.m_aic - r0 < TM ? a.m_aic - r0 : TM);
+    const int64_t wbase = a.row_kbase[r0];
+    const int64_t N = a.row_kbase[r0 + nrows] - wbase;
+    for (int q = threadIdx.x; q <= nrows; q += blockDim.x) rb0[q] = a.row_kbase[r0 + q] - wbase;
+    __syncthreads();
+    const int64_t U = a.win_U[w];
+    const int64_t ntile = (U + TK - 1) / TK;
+    const int32_t dbase = a.win_dptr[w];
+    // columns and value offsets of the dense tiles
+    for (int64_t t = threadIdx.x; t < ntile; t += blockDim.x) {
+        int32_t k = a.trank[wbase + t];
+        if (k < 0) continue;
+        int64_t d = dbase + k;
+        for (int c = 0; c < TK; ++c) {
+            int64_t p = t * TK + c;
+            a.dtile_cols[d * TK + c] = p < U ? a.ucan[wbase + p] : -1;
+        }
+        a.dtile_voff[d] = (int32_t)(a.win_vbase[w] + a.tvoff[wbase + t]);
+    }
+    // bitmap bits
+    for (int64_t e = threadIdx.x; e < N; e += blockDim.x) {
+        int32_t pos = a.epos[wbase + e];
+        int32_t k = a.trank[wbase + pos / TK];
+        if (k < 0) continue;
+        int r = row_slot_of(rb0, nrows, e);
+        int bit = r * TK + pos % TK;
+        atomicOr(a.dtile_bits + (int64_t)(dbase + k) * BW + bit / 32, 1u << (bit % 32));
+    }
+    __syncthreads();
+    // packed values in bitmap order
+    for (int64_t e = threadIdx.x; e < N; e += blockDim.x) {
+        int32_t pos = a.epos[wbase + e];
+        int32_t t = pos / TK;
+        int32_t k = a.trank[wbase + t];
+        if (k < 0) continue;
+        int64_t d = dbase + k;
+        int r = row_slot_of(rb0, nrows, e);
+        int bit = r * TK + pos % TK;
+        const uint32_t* bw = a.dtile_bits + d * BW;
+        int idx = 0;
+        for (int q = 0; q < bit / 32; ++q) idx += __popc(__ldcg(bw + q));
+        idx += __popc(__ldcg(bw + bit / 32) & ((1u << (bit % 32)) - 1u));
+        int64_t vi = (int64_t)a.win_vbase[w] + a.tvoff[wbase + t] + idx;
+        int32_t p = a.eidx[wbase + e];
+        float v = __ldg(a.vals + p);
+        if (a.bf16) {
+            __nv_bfloat16 h = __float2bfloat16_rn(v);
+            reinterpret_cast<uint16_t*>(a.dtile_vals)[vi] = *reinterpret_cast<uint16_t*>(&h);
+        } else {
+            reinterpret_cast<float*>(a.dtile_vals)[vi] = v;
+        }
+        a.pdense[p] = 1;
+    }
+}
+
+// W10: residual CSR (warp per row)
+__global__ void k_residual_scatter(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                   const float* __restrict__ vals, const uint8_t* __restrict__ pdense,
+                                   const int32_t* __restrict__ res_rowptr, int64_t m,
+                                   int32_t* res_col, float* res_val)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int64_t b = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
+        int64_t out = res_rowptr[i];
+        for (int64_t p0 = b; p0 < e; p0 += 32) {
+            int64_t p = p0 + lane;
+            bool keep = p < e && !pdense[p];
+            unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                int64_t o = out + __popc(bal & ((1u << lane) - 1u));
+                res_col[o] = __ldg(colidx + p);
+                res_val[o] = __ldg(vals + p);
+            }
+            out += __popc(bal);
+        }
+    }
+}
+
+__global__ void k_fill_win_rows(const int32_t* __restrict__ aic_rows, int64_t m_aic, int64_t total,
+                                int32_t* win_rows)
+{
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < total;
+         s += (int64_t)gridDim.x * blockDim.x)
+        win_rows[s] = s < m_aic ? aic_rows[s] : -1;
+}
+
+static unsigned wgrid(int64_t n, int threads = 256)
+{
+    int64_t g = ceil_div(n > 0 ? n : 1, threads);
+    return (unsigned)(g < 8 * 152 * 8 ? g : 8 * 152 * 8);
+}
+
+// ---------------------------------------------------------------------------------------------
+// orchestration
+// ---------------------------------------------------------------------------------------------
 ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
 {
-    set_error("dense tiles are not available in this build");
-    return NS_ERR_UNSUPPORTED;
+    const ns_tune_t& t = P->tune;
+    const int64_t m = P->st.m, n = P->st.n, nnz = P->st.nnz;
+    const int TM = t.TM, TK = t.TK, BW = TM * TK / 32;
+    const bool bf16 = P->dtype == NS_BF16;
+
+    // ---- stage 1 arrays: kept rows, column counts, kept lengths ----
+    Arena a1;                          // temporaries of stage 1
+    int64_t* partial = nullptr;
+    int64_t* totals = nullptr;
+    int32_t* aic_rows = nullptr;
+    int32_t* colcount = nullptr;
+    int64_t* row_kbase = nullptr;
+    a1.reserve(&partial, scan_partials(m + 1));
+    a1.reserve(&totals, 8);
+    a1.reserve(&aic_rows, m);
+    a1.reserve(&row_kbase, m + 1);
+    if (t.tau_col > 0) a1.reserve(&colcount, n);
+    NS_TRY(a1.commit(s));
+    NS_CUDA_TRY(cudaMemsetAsync(totals, 0, sizeof(int64_t) * 8, s));
+    NS_TRY(device_scan<int64_t>(KeepLoad{P->rowptr, t.tau_row}, KeepStore{aic_rows}, m, partial,
+                                totals + 0, s));
+    int64_t m_aic_h = 0;
+    NS_CUDA_TRY(cudaMemcpyAsync(&m_aic_h, totals + 0, sizeof m_aic_h, cudaMemcpyDeviceToHost, s));
+    NS_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t m_aic = m_aic_h;
+    if (t.tau_col > 0) {
+        NS_CUDA_TRY(cudaMemsetAsync(colcount, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));
+        if (m_aic > 0) {
+            k_colcount<<<wgrid(m_aic * 32), 256, 0, s>>>(P->rowptr, P->colidx, aic_rows, m_aic, colcount);
+            NS_LAUNCH_CHECK();
+        }
+    }
+    NS_TRY(device_scan<int64_t>(KeptLenLoad{P->rowptr, P->colidx, aic_rows, colcount, t.tau_col},
+                                KeptLenStore{row_kbase}, m_aic, partial, row_kbase + m_aic, s));
+    int64_t nnz_win = 0;
+    if (m_aic > 0) {
+        NS_CUDA_TRY(cudaMemcpyAsync(&nnz_win, row_kbase + m_aic, sizeof nnz_win, cudaMemcpyDeviceToHost, s));
+        NS_CUDA_TRY(cudaStreamSynchronize(s));
+    } else {
+        NS_CUDA_TRY(cudaMemsetAsync(row_kbase, 0, sizeof(int64_t), s));
+    }
+    const int64_t n_win = ceil_div(m_aic, TM);
+    P->st.m_aic = m_aic;
+    P->st.n_win = n_win;
+
+    // ---- stage 2 arrays: plan arrays known by now + window temporaries ----
+    Arena pa;  // plan-owned
+    pa.reserve(&P->aic_rows, m_aic);
+    pa.reserve(&P->win_rows, n_win * TM);
+    pa.reserve(&P->win_dptr, n_win + 1);
+    pa.reserve(&P->dwin, n_win);
+    pa.reserve(&P->dwin_absorb, n_win);
+    pa.reserve(&P->res_rowptr_own, m + 1);
+    pa.reserve(&P->rl_rows, m);
+    pa.reserve(&P->rl_start, m + 1);
+    NS_TRY(pa.commit(s));
+    P->blocks.push_back(pa.take());
+    P->res_rowptr = P->res_rowptr_own;
+
+    Arena tw;  // window temporaries (freed when planning ends)
+    int32_t *ekey, *eidx, *sb0, *sb1, *uasc, *ucnt, *upos, *ucan, *ccnt, *trank, *tvoff, *epos;
+    int32_t *win_U, *win_ndt, *win_ndv, *res_len;
+    int64_t *win_res, *win_vbase, *part2;
+    int8_t* row_state;
+    int64_t* dcost;
+    uint8_t* pdense;
+    for (int32_t** q : {&ekey, &eidx, &sb0, &sb1, &uasc, &ucnt, &upos, &ucan, &ccnt, &trank, &tvoff, &epos})
+        tw.reserve(q, nnz_win);
+    tw.reserve(&win_U, n_win);
+    tw.reserve(&win_ndt, n_win);
+    tw.reserve(&win_ndv, n_win);
+    tw.reserve(&win_res, n_win);
+    tw.reserve(&win_vbase, n_win + 1);
+    tw.reserve(&res_len, m);
+    tw.reserve(&part2, scan_partials(m + 1));
+    tw.reserve(&row_state, m);
+    tw.reserve(&dcost, n_win);
+    tw.reserve(&pdense, nnz);
+    NS_TRY(tw.commit(s));
+    W->temp = tw.take();
+    W->row_state = row_state;
+    W->dcost = dcost;
+
+    if (m_aic > 0) {
+        NS_CUDA_TRY(cudaMemcpyAsync(P->aic_rows, aic_rows, sizeof(int32_t) * m_aic, cudaMemcpyDeviceToDevice, s));
+        k_fill_win_rows<<<wgrid(n_win * TM), 256, 0, s>>>(aic_rows, m_aic, n_win * TM, P->win_rows);
+        NS_LAUNCH_CHECK();
+        k_gather_window_elems<<<wgrid(m_aic * 32), 256, 0, s>>>(P->rowptr, P->colidx, aic_rows, m_aic,
+                                                               row_kbase, colcount, t.tau_col, ekey, eidx);
+        NS_LAUNCH_CHECK();
+    }
+    k_res_len_free_rows<<<wgrid(m), 256, 0, s>>>(P->rowptr, m, t.tau_row, res_len);
+    NS_LAUNCH_CHECK();
+    if (n_win > 0) {
+        WinArgs wa{P->rowptr, aic_rows, row_kbase, ekey, m_aic, TM, TK, t.tau_tile, t.col_order,
+                   sb0, sb1, uasc, ucnt, upos, ucan, ccnt, trank, tvoff, epos,
+                   win_U, win_ndt, win_ndv, win_res, res_len};
+        k_window_compact<<<(unsigned)n_win, kWinThreads, 0, s>>>(wa);
+        NS_LAUNCH_CHECK();
+    }
+
+    // ---- W6: scans ----
+    NS_CUDA_TRY(cudaMemsetAsync(totals, 0, sizeof(int64_t) * 8, s));
+    NS_TRY(device_scan<int64_t>(I32Load{win_ndt}, PtrStore32{P->win_dptr}, n_win, partial, totals + 1, s));
+    NS_TRY(device_scan<int64_t>(I32Load{win_ndv}, PtrStore64{win_vbase}, n_win, partial, totals + 2, s));
+    NS_TRY(device_scan<int64_t>(DenseWinLoad{win_ndt}, DenseWinStore{P->dwin}, n_win, partial, totals + 3, s));
+    NS_TRY(device_scan<int64_t>(I32Load{res_len}, PtrStore32{P->res_rowptr_own}, m, part2, totals + 4, s));
+    int64_t ht[8];
+    NS_CUDA_TRY(cudaMemcpyAsync(ht, totals, sizeof ht, cudaMemcpyDeviceToHost, s));
+    NS_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t n_dtiles = ht[1], n_dvals = ht[2], n_dwin = ht[3], n_res = ht[4];
+    P->st.n_dtiles = n_dtiles;
+    P->st.n_dvals = n_dvals;
+    P->st.n_dwin = n_dwin;
+    P->st.n_res = n_res;
+    // scan totals at the end of the pointer arrays
+    {
+        int32_t v32 = (int32_t)n_dtiles;
+        NS_CUDA_TRY(cudaMemcpyAsync(P->win_dptr + n_win, &v32, sizeof v32, cudaMemcpyHostToDevice, s));
+        int32_t r32 = (int32_t)n_res;
+        NS_CUDA_TRY(cudaMemcpyAsync(P->res_rowptr_own + m, &r32, sizeof r32, cudaMemcpyHostToDevice, s));
+    }
+
+    // ---- W7: dense windows, ownership; W8: residual list ----
+    NS_CUDA_TRY(cudaMemsetAsync(row_state, 0, (size_t)(m > 0 ? m : 1), s));
+    if (n_dwin > 0) {
+        k_dense_windows<<<wgrid(n_dwin), 256, 0, s>>>(P->dwin, n_dwin, win_ndt, win_res, aic_rows, m_aic,
+                                                      TM, TK, t.absorb_cap, t.cost_tc, t.cost_res,
+                                                      P->dwin_absorb, dcost, row_state);
+        NS_LAUNCH_CHECK();
+    }
+    NS_TRY(device_scan<int64_t>(RlLoad{row_state, res_len}, RlStore{P->rl_rows, P->rl_start}, m, part2,
+                                totals + 5, s));
+
+    // ---- W9/W10: dense tiles and the residual CSR ----
+    Arena pb;
+    pb.reserve(&P->dtile_cols, n_dtiles * TK);
+    pb.reserve(&P->dtile_bits, n_dtiles * BW);
+    pb.reserve(&P->dtile_voff, n_dtiles + 1);
+    pb.reserve_bytes(&P->dtile_vals, (size_t)(n_dvals > 0 ? n_dvals : 1) * (bf16 ? 2 : 4));
+    pb.reserve(&P->res_col_own, n_res);
+    pb.reserve(&P->res_val_own, n_res);
+    NS_TRY(pb.commit(s));
+    P->blocks.push_back(pb.take());
+    P->res_col = P->res_col_own;
+    P->res_val = P->res_val_own;
+    NS_CUDA_TRY(cudaMemsetAsync(P->dtile_bits, 0, sizeof(uint32_t) * (n_dtiles * BW > 0 ? n_dtiles * BW : 1), s));
+    NS_CUDA_TRY(cudaMemsetAsync(P->dtile_vals, 0, (size_t)(n_dvals > 0 ? n_dvals : 1) * (bf16 ? 2 : 4), s));
+    NS_CUDA_TRY(cudaMemsetAsync(pdense, 0, (size_t)(nnz > 0 ? nnz : 1), s));
+    {
+        int32_t v32 = (int32_t)n_dvals;
+        NS_CUDA_TRY(cudaMemcpyAsync(P->dtile_voff + n_dtiles, &v32, sizeof v32, cudaMemcpyHostToDevice, s));
+    }
+    if (n_dtiles > 0) {
+        EmitArgs ea{row_kbase, eidx, epos, ucan, trank, tvoff, win_U, win_ndt, P->win_dptr, win_vbase,
+                    P->vals, m_aic, TM, TK, bf16 ? 1 : 0, P->dtile_cols, P->dtile_bits, P->dtile_voff,
+                    P->dtile_vals, pdense};
+        k_emit_tiles<<<(unsigned)n_win, kWinThreads, 0, s>>>(ea);
+        NS_LAUNCH_CHECK();
+    }
+    if (m > 0) {
+        k_residual_scatter<<<wgrid(m * 32), 256, 0, s>>>(P->rowptr, P->colidx, P->vals, pdense,
+                                                          P->res_rowptr_own, m, P->res_col_own,
+                                                          P->res_val_own);
+        NS_LAUNCH_CHECK();
+    }
+    int64_t rl_tot = 0;
+    NS_CUDA_TRY(cudaMemcpyAsync(&rl_tot, totals + 5, sizeof rl_tot, cudaMemcpyDeviceToHost, s));
+    NS_CUDA_TRY(cudaStreamSynchronize(s));
+    P->st.n_rl = rl_tot >> 32;
+    P->st.T = rl_tot & 0xffffffffLL;
+    {
+        int32_t T32 = (int32_t)P->st.T;
+        NS_CUDA_TRY(cudaMemcpyAsync(P->rl_start + P->st.n_rl, &T32, sizeof T32, cudaMemcpyHostToDevice, s));
+        NS_CUDA_TRY(cudaStreamSynchronize(s));  // the host values above must outlive the copies
+    }
+    a1.release(s);
+    return NS_OK;
 }
 
 }  // namespace ns

@@ -116,6 +116,10 @@ def make_workload(name: str, seed: int):
         A, B = synth.config_attention(seed)
         desc = {"workload": "block-sparse-attention-32768-K128-fp32", "m": A["m"], "n": A["n"],
                 "nnz": A.nnz, "K": 128, "b_dtype": "f32", "seed": seed}
+    elif name == "attention-bf16":
+        A, B = synth.config_attention(seed)
+        desc = {"workload": "block-sparse-attention-32768-K128-bf16", "m": A["m"], "n": A["n"],
+                "nnz": A.nnz, "K": 128, "b_dtype": "bf16", "seed": seed}
     elif name == "small":
         A, B = synth.config_small(seed)
         desc = {"workload": "uniform-4096-16nnz-K32-fp32", "m": A["m"], "n": A["n"],
@@ -140,18 +144,18 @@ def cpu_sample_rows(A, target_nnz: int, seed: int = 7):
     return rows, int(lens.sum())
 
 
-def run_cpu_oracle(A, B, K, seconds_budget: float, threads: int):
+def run_cpu_oracle(A, B, K, seconds_budget: float, threads: int, bf16: bool = False):
     """Time the oracle, as it stands, on a row sample sized for ~seconds_budget of CPU work."""
     import oracle
     rows, nnz_s = cpu_sample_rows(A, 200_000)
     t0 = time.perf_counter()
-    oracle.spmm(A, B, rows=rows, threads=threads)
+    oracle.spmm(A, B, rows=rows, threads=threads, b_bf16=bf16)
     t1 = time.perf_counter()
     rate = 2.0 * nnz_s * K / max(t1 - t0, 1e-9)   # flop/s on the probe
     target = int(min(A.nnz, max(200_000, rate * seconds_budget / (2.0 * K))))
     rows, nnz_s = cpu_sample_rows(A, target, seed=11)
     t0 = time.perf_counter()
-    oracle.spmm(A, B, rows=rows, threads=threads)
+    oracle.spmm(A, B, rows=rows, threads=threads, b_bf16=bf16)
     dt = time.perf_counter() - t0
     return {"value": 2.0 * nnz_s * K / dt / 1e9, "unit": "GFLOP/s", "cores": threads,
             "kind": "oracle",
@@ -172,7 +176,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="powerlaw", choices=["powerlaw", "attention", "small"])
+    ap.add_argument("--workload", default="powerlaw",
+                    choices=["powerlaw", "attention", "attention-bf16", "small", "batched", "serve"])
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrivals per second")
+    ap.add_argument("--duration", type=float, default=5.0, help="serve: seconds of arrivals")
+    ap.add_argument("--pool", type=int, default=64, help="serve: graphs in the pool")
     ap.add_argument("--tau", default="auto", help="'auto' (autotuner), 'inf' or an integer")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
@@ -213,6 +221,10 @@ def main():
     import torch
     import torch.distributed as dist
 
+    if args.workload == "batched":
+        return bench_batched(args, threads)
+    if args.workload == "serve":
+        return bench_serve(args, threads)
     if ws > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
@@ -221,8 +233,15 @@ def main():
 
     A, B, desc = make_workload(args.workload, args.seed + rank)
     K = B.shape[1]
+    bf16 = desc["b_dtype"] == "bf16"
+    DT = ns.NS_BF16 if bf16 else ns.NS_F32
     At = {k: (torch.from_numpy(v).to(dev) if isinstance(v, np.ndarray) else v) for k, v in A.items()}
-    Bt = torch.from_numpy(B).to(dev)
+    if bf16:
+        import synth
+        B = synth.bf16_bits(B)
+        Bt = torch.from_numpy(B.view(np.int16)).to(dev).view(torch.bfloat16)
+    else:
+        Bt = torch.from_numpy(B).to(dev)
     Ct = torch.empty((A["m"], K), device=dev)
     stream = torch.cuda.current_stream()
 
@@ -237,14 +256,14 @@ def main():
         tune_src = f"fixed tau={args.tau}"
     else:
         try:
-            tune = ns.autotune(At, K, ns.NS_F32)
+            tune = ns.autotune(At, K, DT)
             tune_src = "autotuned"
         except Exception as e:  # autotuner unavailable: pure CUDA-core plan
             tune.tau_tile = ns.NS_TAU_INF
             tune_src = f"default (autotune unavailable: {str(e)[:60]})"
 
     def step(ev=None):
-        p = ns.spmm_plan(At, K, ns.NS_F32, tune)
+        p = ns.spmm_plan(At, K, DT, tune)
         if ev is not None:
             ev[0].record(stream)
         p.execute(Bt, Ct)
@@ -255,7 +274,7 @@ def main():
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
-    with ns.spmm_plan(At, K, ns.NS_F32, tune) as p:
+    with ns.spmm_plan(At, K, DT, tune) as p:
         st = p.stats()
 
     exec_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -286,7 +305,7 @@ def main():
     flops = 2.0 * A.nnz * K
     value = flops * ws / (ms_step * 1e-3) / 1e9
     hbm, peak_src = _peaks()
-    alg_bytes, n_touched = algorithmic_bytes(A, K, 4)
+    alg_bytes, n_touched = algorithmic_bytes(A, K, 2 if bf16 else 4)
     achieved = alg_bytes / (exec_ms * 1e-3) / 1e9
 
     # ---- e2e: host buffers through ns_spmm_host ----
@@ -297,11 +316,11 @@ def main():
         Bh = torch.from_numpy(B).pin_memory().numpy()
         Ch = torch.empty((A["m"], K), dtype=torch.float32).pin_memory().numpy()
         for _ in range(2):
-            ns.spmm_host(Ah, Bh, Ch, ns.NS_F32, tune)
+            ns.spmm_host(Ah, Bh, Ch, DT, tune)
         n_e2e = max(3, min(args.steps, 10))
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            ns.spmm_host(Ah, Bh, Ch, ns.NS_F32, tune)
+            ns.spmm_host(Ah, Bh, Ch, DT, tune)
         dt = (time.perf_counter() - t0) / n_e2e
         h2d = 4 * (A["m"] + 1) + 8 * A.nnz + B.nbytes
         e2e = {"value": flops * ws / dt / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
@@ -314,12 +333,12 @@ def main():
         return
     cpu = None
     if not args.no_cpu:
-        cpu = run_cpu_oracle(A, B, K, 12.0, threads)
+        cpu = run_cpu_oracle(A, B, K, 12.0, threads, bf16)
     out = {
         "metric": "SpMM GFLOP/s (2*nnz*K/s) & % HBM roofline",
         "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if bf16 else "f32", "data": "synthetic",
         "config": dict(desc, parallelism=f"replicas x{ws}", l2="inputs larger than L2 (A+B+C 1.16 GB)",
                        step="device plan + one persistent execute launch", tune=tune.as_dict(),
                        tune_source=tune_src, plan=st),
@@ -337,6 +356,183 @@ def main():
     print(json.dumps(out))
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------------
+# batched form: 512 uneven graphs, K = 64, one persistent launch replayed from a CUDA graph
+# ---------------------------------------------------------------------------------------------
+def bench_batched(args, threads):
+    import torch
+    import oracle
+    import synth
+    import paper_2606_22482_gb300 as ns
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    graphs, Bs = synth.config_batched(args.seed)
+    K = 64
+    Ad = [{k: (torch.from_numpy(v).to(dev) if isinstance(v, np.ndarray) else v) for k, v in g.items()}
+          for g in graphs]
+    Bd = [torch.from_numpy(b).to(dev) for b in Bs]
+    Cd = [torch.empty((g["m"], K), device=dev) for g in graphs]
+    nnz = sum(g.nnz for g in graphs)
+    # tune on the largest graph (project autotuner), applied to every graph
+    big = int(np.argmax([g.nnz for g in graphs]))
+    try:
+        tune = ns.autotune(Ad[big], K, ns.NS_F32)
+        src = "autotuned on the largest graph"
+    except Exception as e:
+        tune = ns.tune_default()
+        src = f"default ({str(e)[:40]})"
+    t0 = time.perf_counter()
+    bt = ns.Batch(Ad, [K] * len(graphs), ns.NS_F32, tune)
+    plan_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        bt.execute(Bd, Cd)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ns.launch_count()
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            bt.execute(Bd, Cd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # parity on a sample of graphs
+    errs = []
+    for g in range(0, len(graphs), 37):
+        errs.append(oracle.rel_frobenius(Cd[g].cpu().numpy(), oracle.spmm(graphs[g], Bs[g], threads=threads)))
+    n_touched = sum(int(np.count_nonzero(np.bincount(g["colidx"], minlength=g["n"]))) for g in graphs)
+    alg = sum(4 * (g["m"] + 1) + 8 * g.nnz + 4 * g["m"] * K for g in graphs) + 4 * K * n_touched
+    hbm, src_pk = _peaks()
+    print(json.dumps({
+        "metric": "SpMM GFLOP/s (2*nnz*K/s), batched form", "value": 2.0 * nnz * K / (ms * 1e-3) / 1e9,
+        "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched-512-graphs-K64-fp32", "graphs": len(graphs), "nnz": nnz,
+                   "step": "one persistent launch (CUDA graph replay) over all graphs",
+                   "tune": tune.as_dict(), "tune_source": src, "plan_s": plan_s, **bt.stats()},
+        "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": alg / (ms * 1e-3) / 1e9 / hbm, "traffic": None, "peak_source": src_pk},
+        "max_rel_frobenius_sampled": max(errs), "gpu_launches": ns.launch_count() - l0,
+        "clocks": clk.summary()}))
+
+
+# ---------------------------------------------------------------------------------------------
+# served form: open-loop Poisson arrivals, continuous batching vs one request at a time
+# ---------------------------------------------------------------------------------------------
+def bench_serve(args, threads):
+    import torch
+    import oracle
+    import synth
+    import paper_2606_22482_gb300 as ns
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(args.seed)
+    sizes = synth.serve_pool_sizes(args.pool, args.seed)
+    graphs = [synth.serve_graph(int(n), seed=1000 + i) for i, n in enumerate(sizes)]
+    n_req = int(args.rate * args.duration)
+    arr = np.cumsum(rng.exponential(1.0 / args.rate, size=n_req))
+    req_g = rng.integers(0, len(graphs), size=n_req)
+    req_K = rng.choice([32, 64, 128], size=n_req)
+    req_bf = rng.integers(0, 2, size=n_req).astype(bool)
+    # pinned operands: one B per (graph, K, dtype); a ring of C buffers per (graph, K)
+    Bbuf, Cring = {}, {}
+    ring = 8
+    for g, K, bf in set(zip(req_g.tolist(), req_K.tolist(), req_bf.tolist())):
+        b = synth.dense_b(graphs[g]["n"], K, seed=g * 7 + K)
+        if bf:
+            t = torch.from_numpy(synth.bf16_bits(b).view(np.int16)).pin_memory()
+            Bbuf[(g, K, bf)] = (t, t.numpy().view(np.uint16), b)
+        else:
+            t = torch.from_numpy(b).pin_memory()
+            Bbuf[(g, K, bf)] = (t, t.numpy(), b)
+        if (g, K) not in Cring:
+            Cring[(g, K)] = [torch.empty((graphs[g]["m"], K), dtype=torch.float32).pin_memory()
+                             for _ in range(ring)]
+    flops = float(sum(2.0 * graphs[g].nnz * K for g, K in zip(req_g, req_K)))
+
+    def run_served(max_inflight):
+        sv = ns.Server(hbm_budget_bytes=16 << 30, max_inflight=max_inflight, max_queue=1 << 16)
+        gids = [sv.register(g) for g in graphs]
+        # warm: plan every (graph, K, dtype) once so plans are resident (serving keeps them)
+        warm = []
+        for key in Bbuf:
+            g, K, bf = key
+            warm.append(sv.submit(gids[g], Bbuf[key][1], Cring[(g, K)][0].numpy(),
+                                  ns.NS_BF16 if bf else ns.NS_F32))
+        for t in warm:
+            while not sv.poll(t)[0]:
+                time.sleep(0.0002)
+        use = {k: 0 for k in Cring}
+        tickets = [None] * n_req
+        lat = np.zeros(n_req)
+        pending = {}
+        t0 = ns.now()
+        i = 0
+        while i < n_req or pending:
+            now = ns.now() - t0
+            while i < n_req and arr[i] <= now:
+                g, K, bf = int(req_g[i]), int(req_K[i]), bool(req_bf[i])
+                Cb = Cring[(g, K)][use[(g, K)] % ring]
+                use[(g, K)] += 1
+                tk = sv.submit(gids[g], Bbuf[(g, K, bf)][1], Cb.numpy(), ns.NS_BF16 if bf else ns.NS_F32,
+                               t_arrival=t0 + arr[i])
+                pending[tk] = i
+                i += 1
+            for tk in list(pending):
+                done, st = sv.poll(tk)
+                if done:
+                    j = pending.pop(tk)
+                    lat[j] = st["t_done"] - (t0 + arr[j])
+            time.sleep(0.00005)
+        wall = ns.now() - t0
+        sv.close()
+        return lat, wall
+
+    def run_plain():
+        """the same trace, one request at a time through ns_spmm_host (plan + execute + copies)"""
+        lat = np.zeros(n_req)
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            now = time.perf_counter() - t0
+            if arr[i] > now:
+                time.sleep(arr[i] - now)
+            g, K, bf = int(req_g[i]), int(req_K[i]), bool(req_bf[i])
+            ns.spmm_host(graphs[g], Bbuf[(g, K, bf)][1], Cring[(g, K)][0].numpy(), ns.NS_BF16 if bf else ns.NS_F32)
+            lat[i] = time.perf_counter() - t0 - arr[i]
+        return lat, time.perf_counter() - t0
+
+    lat_s, wall_s = run_served(64)
+    lat_p, wall_p = run_plain()
+    # accuracy spot check of served results (fresh run of a few requests)
+    errs = []
+    sv = ns.Server(hbm_budget_bytes=16 << 30)
+    gids = [sv.register(g) for g in graphs]
+    for i in range(0, n_req, max(1, n_req // 8)):
+        g, K, bf = int(req_g[i]), int(req_K[i]), bool(req_bf[i])
+        C = np.empty((graphs[g]["m"], K), dtype=np.float32)
+        tk = sv.submit(gids[g], Bbuf[(g, K, bf)][1], C, ns.NS_BF16 if bf else ns.NS_F32)
+        while not sv.poll(tk)[0]:
+            time.sleep(0.0002)
+        ref = oracle.spmm(graphs[g], Bbuf[(g, K, bf)][1], b_bf16=bf, threads=threads)
+        errs.append((oracle.rel_frobenius(C, ref), bf))
+    sv.close()
+    pct = lambda a, q: float(np.percentile(a, q) * 1e3)
+    print(json.dumps({
+        "metric": "served SpMM throughput & p50/p99 latency", "value": flops / wall_s / 1e9,
+        "unit": "GFLOP/s", "n_gpus": 1, "higher_is_better": True, "dtype": "mixed f32/bf16",
+        "data": "synthetic",
+        "config": {"workload": f"serve-poisson-{args.rate:g}/s-{args.duration:g}s-pool{args.pool}",
+                   "requests": n_req, "K": "{32,64,128}", "b_dtype": "50/50 f32/bf16",
+                   "graph_nodes_median": float(np.median(sizes)), "graph_nodes_max": int(sizes.max())},
+        "served": {"requests_per_s": n_req / wall_s, "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99),
+                   "GFLOP_per_s": flops / wall_s / 1e9},
+        "plain": {"requests_per_s": n_req / wall_p, "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
+                  "GFLOP_per_s": flops / wall_p / 1e9, "how": "one request at a time, ns_spmm_host"},
+        "max_rel_frobenius": {"f32": max([e for e, b in errs if not b] or [0.0]),
+                              "bf16": max([e for e, b in errs if b] or [0.0])}}))
 
 
 if __name__ == "__main__":

@@ -155,3 +155,125 @@ def spmm_host(A: dict, B: np.ndarray, C: np.ndarray, b_dtype: int = NS_F32,
 
 def launch_count() -> int:
     return int(lib.ns_launch_count())
+
+
+def autotune(A: dict, K: int, b_dtype: int = NS_F32, stream=None, report: bool = False):
+    """ns_autotune on a device CSR: returns the chosen Tune (and the dry-run report if asked)."""
+    c, keep = _csr_struct(A, True)
+    t = Tune()
+    rep = _abi.TuneReport()
+    check(lib.ns_autotune(ctypes.byref(c), int(K), int(b_dtype), _stream_handle(stream),
+                          ctypes.byref(t), ctypes.byref(rep)))
+    if report:
+        return t, {f: getattr(rep, f) for f, _ in _abi.TuneReport._fields_}
+    return t
+
+
+class Batch:
+    """ns_batch_*: many SpMMs in one persistent launch replayed from a CUDA graph."""
+
+    def __init__(self, As: list, Ks: list, b_dtype: int = NS_F32, tune: Tune | None = None,
+                 stream=None):
+        structs, self._keep = [], []
+        for A in As:
+            c, keep = _csr_struct(A, True)
+            structs.append(c)
+            self._keep.append(keep)
+        arr = (_abi.Csr * len(structs))(*structs)
+        ks = (ctypes.c_int32 * len(Ks))(*[int(k) for k in Ks])
+        self._h = ctypes.c_void_p()
+        self.Ks = [int(k) for k in Ks]
+        self.dtype = int(b_dtype)
+        check(lib.ns_batch_plan(arr, len(structs), ks, int(b_dtype),
+                                ctypes.byref(tune) if tune is not None else None,
+                                _stream_handle(stream), ctypes.byref(self._h)))
+
+    def execute(self, Bs: list, Cs: list, stream=None) -> None:
+        n = len(Bs)
+        bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in Bs])
+        cp = (ctypes.c_void_p * n)(*[c.data_ptr() for c in Cs])
+        check(lib.ns_batch_execute(self._h, bp, cp, _stream_handle(stream)))
+
+    def stats(self) -> dict:
+        ni, ng = ctypes.c_int64(), ctypes.c_int64()
+        check(lib.ns_batch_stats(self._h, ctypes.byref(ni), ctypes.byref(ng)))
+        return {"n_items": ni.value, "n_graphs": ng.value}
+
+    def close(self) -> None:
+        if self._h:
+            lib.ns_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """ns_serve_*: continuous batching of SpMM requests (host operands, device-resident plans)."""
+
+    def __init__(self, hbm_budget_bytes: int = 8 << 30, max_inflight: int = 64,
+                 max_queue: int = 4096, max_graphs: int = 1024, tune: Tune | None = None):
+        cfg = _abi.ServeCfg()
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        cfg.max_inflight = int(max_inflight)
+        cfg.max_queue = int(max_queue)
+        cfg.max_graphs = int(max_graphs)
+        cfg.tune = tune if tune is not None else tune_default()
+        self._h = ctypes.c_void_p()
+        check(lib.ns_serve_create(ctypes.byref(cfg), ctypes.byref(self._h)))
+        self._graphs = []
+        self._live = {}
+
+    def register(self, A: dict) -> int:
+        c, keep = _csr_struct(A, False)
+        gid = ctypes.c_int32()
+        check(lib.ns_serve_register_graph(self._h, ctypes.byref(c), ctypes.byref(gid)))
+        return int(gid.value)
+
+    def submit(self, graph_id: int, B: np.ndarray, C: np.ndarray, b_dtype: int = NS_F32,
+               t_arrival: float | None = None) -> int:
+        """Queue C = A_g @ B; B (uint16 BF16 bits or float32) and C (float32) stay alive until done."""
+        r = _abi.Request()
+        r.graph_id = int(graph_id)
+        r.K = int(B.shape[1])
+        r.b_dtype = int(b_dtype)
+        r.B = ctypes.c_void_p(B.ctypes.data)
+        r.C = ctypes.c_void_p(C.ctypes.data)
+        r.t_arrival = float(t_arrival if t_arrival is not None else now())
+        t = ctypes.c_uint64()
+        check(lib.ns_serve_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        self._live[int(t.value)] = (B, C)
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """(done, stats dict or None); raises NsError if the request failed."""
+        done = ctypes.c_int()
+        st = _abi.ReqStats()
+        try:
+            check(lib.ns_serve_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(done), ctypes.byref(st)))
+        finally:
+            if done.value:
+                self._live.pop(ticket, None)
+        if not done.value:
+            return False, None
+        return True, {f: getattr(st, f) for f, _ in _abi.ReqStats._fields_}
+
+    def close(self) -> None:
+        if self._h:
+            lib.ns_serve_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def now() -> float:
+    """The serving clock (seconds), for request arrival stamps."""
+    return float(lib.ns_serve_now())

@@ -48,11 +48,13 @@ struct Batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t graph_stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream for the one-time capture
     int64_t n_items = 0;
     ~Batch()
     {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         for (Plan* p : plans) delete p;
         cudaStreamSynchronize(graph_stream);
         for (auto& b : blocks)
@@ -220,21 +222,25 @@ ns_status_t ns_batch_execute(ns_batch_t b, const void* const* Bs, float* const* 
         // capture every group's persistent launch once; later calls replay the graph
         for (auto& G : Bt->groups)  // occupancy queries and attributes outside the capture
             NS_TRY(exec_prepare(G.n_items, G.K, G.TM, G.TK, Bt->dtype == NS_BF16, Bt->hint, G.dense, &G.grid));
-        NS_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        // the caller's stream may be the legacy default stream, which cannot be captured: record
+        // the launches on a private stream once; the graph then replays on the caller's stream
+        if (!Bt->cap_stream) NS_CUDA_TRY(cudaStreamCreateWithFlags(&Bt->cap_stream, cudaStreamNonBlocking));
+        NS_CUDA_TRY(cudaStreamBeginCapture(Bt->cap_stream, cudaStreamCaptureModeThreadLocal));
         ns_status_t r = NS_OK;
         for (auto& G : Bt->groups) {
             r = exec_launch(G.descs_dev, G.queue, G.queue_desc, G.n_items, G.ctrl, G.K, G.TM, G.TK,
-                            Bt->dtype == NS_BF16, Bt->hint, G.dense, &G.grid, st);
+                            Bt->dtype == NS_BF16, Bt->hint, G.dense, &G.grid, Bt->cap_stream);
             if (r != NS_OK) break;
         }
         cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        cudaError_t e = cudaStreamEndCapture(Bt->cap_stream, &graph);
         if (r != NS_OK) return r;
         if (e != cudaSuccess) {
             set_error("stream capture failed: %s", cudaGetErrorString(e));
             return NS_ERR_CUDA;
         }
         Bt->graph = graph;
+        count_launch(-(int64_t)Bt->groups.size());  // recorded, not launched: counted at replay
         NS_CUDA_TRY(cudaGraphInstantiate(&Bt->exec, graph, 0));
     }
     NS_CUDA_TRY(cudaGraphLaunch(Bt->exec, st));

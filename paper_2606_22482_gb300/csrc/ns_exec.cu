@@ -235,6 +235,144 @@ __device__ __forceinline__ void group_reduce(float4 (&acc)[VPL])
         }
 }
 
+// split-row delivery out of line (rare): keeps the inlined row flush of the stream path small
+template <int VPL, bool HINT>
+__device__ __noinline__ void deliver_split_row(const ExecDesc& D, int32_t row, int32_t s, int32_t c,
+                                               float4 a0, float4 a1, int lane, uint64_t pol_first)
+{
+    const int nv = D.K >> 2;
+    const int32_t np = __ldg(D.split_np + s);
+    const int32_t piece = c - __ldg(D.split_base + s);
+    float* slot0 = D.slots + (int64_t)__ldg(D.split_slot + s) * D.K;
+    if (lane < nv) __stcg(reinterpret_cast<float4*>(slot0 + (int64_t)piece * D.K + 4 * lane), a0);
+    if (VPL > 1 && lane + 32 < nv)
+        __stcg(reinterpret_cast<float4*>(slot0 + (int64_t)piece * D.K + 4 * (lane + 32)), a1);
+    __threadfence();
+    __syncwarp();
+    int old = 0;
+    if (lane == 0) old = atomicAdd(D.split_cnt + s, 1);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    if (old != np - 1) return;
+    __threadfence();
+    float* crow = D.C + (int64_t)row * D.ldc;
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) {
+        const int v = lane + 32 * q;
+        if (v < nv) {
+            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int p = 0; p < np; ++p)
+                sum = f4_add(sum, __ldcg(reinterpret_cast<const float4*>(slot0 + (int64_t)p * D.K + 4 * v)));
+            st_c4<HINT>(crow + 4 * v, sum, pol_first);
+        }
+    }
+    if (lane == 0) atomicExch(D.split_cnt + s, 0);
+}
+
+// Residual chunk when the residual list is every row in order (no dense windows) and K >= 128
+// (one nonzero per warp step, 32 lanes x 4 columns x VPL).  The chunk's nonzeros are then one
+// contiguous stream: (col, val) batches of 32 are loaded one batch ahead, row ends and split ids
+// of 32 rows at a time, and U gathered B rows stay in flight across row boundaries.  Removes the
+// per-row chain of dependent loads (row pointer -> column ids -> B row).
+template <int VPL, bool BF16, bool HINT>
+__device__ void residual_chunk_stream(const ExecDesc& D, int32_t c, int lane, const Policies& pol)
+{
+    constexpr int U = VPL == 1 ? 8 : 4;
+    const int nv = D.K >> 2;
+    const int64_t b0 = __ldg(D.chunk_b + c), b1 = __ldg(D.chunk_b + c + 1);
+    const int64_t k0 = __ldg(D.chunk_k0 + c);
+    // last row with a merge item in [b0, b1): the row holding b1 - 1
+    int64_t kL = (c + 1 < D.n_chunks) ? (int64_t)__ldg(D.chunk_k0 + c + 1) : (int64_t)D.n_rl - 1;
+    if (kL > k0 && (int64_t)__ldg(D.res_rowptr + kL) + kL >= b1) --kL;
+    const int64_t zA = b0 - k0;                              // first nonzero of the chunk
+    const int64_t eL = __ldg(D.res_rowptr + kL + 1);
+    const int64_t zZ = (eL + kL >= b1) ? b1 - kL : eL;       // end of the chunk's nonzeros
+    if (k0 < 0 || kL >= D.n_rl || zA < 0 || zZ > D.n_res || zA > zZ + 1) {
+        if (lane == 0) atomicOr(D.status, kStatusInternal);
+        return;
+    }
+    int64_t kb = k0;  // first row of the lanes' metadata window
+    int32_t my_end = kb + lane <= kL ? __ldg(D.res_rowptr + kb + lane + 1) : 0x7fffffff;
+    int32_t my_split = kb + lane <= kL ? __ldg(D.row_split + kb + lane) : -1;
+    int64_t k = k0;
+    int64_t rend = __shfl_sync(0xffffffffu, my_end, 0);
+    float4 acc[VPL];
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    // deliver row k (its nonzeros in this chunk are summed in acc) and move to row k + 1
+    auto flush = [&]() {
+        const int32_t s = __shfl_sync(0xffffffffu, my_split, (int)(k - kb));
+        if (s < 0) {
+            float* crow = D.C + k * D.ldc;
+#pragma unroll
+            for (int q = 0; q < VPL; ++q) {
+                const int v = lane + 32 * q;
+                if (v < nv) st_c4<HINT>(crow + 4 * v, acc[q], pol.first);
+            }
+        } else {
+            deliver_split_row<VPL, HINT>(D, (int32_t)k, s, c, acc[0], acc[VPL > 1 ? VPL - 1 : 0], lane,
+                                         pol.first);
+        }
+#pragma unroll
+        for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ++k;
+        if (k - kb == 32) {
+            kb = k;
+            my_end = kb + lane <= kL ? __ldg(D.res_rowptr + kb + lane + 1) : 0x7fffffff;
+            my_split = kb + lane <= kL ? __ldg(D.row_split + kb + lane) : -1;
+        }
+        rend = __shfl_sync(0xffffffffu, my_end, (int)(k - kb));
+    };
+
+    int32_t mc = 0, nc_ = 0;
+    float mv = 0.f, nv_ = 0.f;
+    if (zA + lane < zZ) {
+        mc = ld_stream_i32<HINT>(D.res_col + zA + lane, pol.first);
+        mv = ld_stream_f32<HINT>(D.res_val + zA + lane, pol.first);
+    }
+    for (int64_t zb = zA; zb < zZ; zb += 32) {
+        const int cnt = (int)(zZ - zb < 32 ? zZ - zb : 32);
+        // next batch of column ids and values, one batch ahead
+        if (zb + 32 + lane < zZ) {
+            nc_ = ld_stream_i32<HINT>(D.res_col + zb + 32 + lane, pol.first);
+            nv_ = ld_stream_f32<HINT>(D.res_val + zb + 32 + lane, pol.first);
+        }
+        if (lane < cnt && (unsigned)mc >= (unsigned)D.n) {  // guard: never gather outside B
+            atomicOr(D.status, kStatusInternal);
+            mc = 0;
+            mv = 0.f;
+        }
+        for (int j0 = 0; j0 < cnt; j0 += U) {
+            float4 b[U][VPL];
+            float val[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = j0 + u;
+                const int32_t col = __shfl_sync(0xffffffffu, mc, j & 31);
+                val[u] = __shfl_sync(0xffffffffu, mv, j & 31);
+#pragma unroll
+                for (int q = 0; q < VPL; ++q) {
+                    const int v = lane + 32 * q;
+                    b[u][q] = (j < cnt && v < nv) ? ld_b4<BF16, HINT>(D.B, (int64_t)col * D.ldb + 4 * v, pol.last)
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (j0 + u < cnt) {
+                    const int64_t z = zb + j0 + u;
+                    while (z >= rend) flush();
+#pragma unroll
+                    for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(val[u], b[u][q], acc[q]);
+                }
+            }
+        }
+        mc = nc_;
+        mv = nv_;
+    }
+    while (k <= kL) flush();  // the last row (whole or a piece) and trailing empty rows
+}
+
 // one merge-path chunk c of the residual (one warp)
 template <int L, int VPL, bool BF16, bool HINT>
 __device__ void residual_chunk(const ExecDesc& D, int32_t c, int lane, const Policies& pol)
@@ -304,7 +442,12 @@ __global__ void __launch_bounds__(kExecThreads) k_exec(const ExecDesc* __restric
             dense_item<L, VPL, BF16, HINT>(D, it, smem_raw, pol);
         } else {
             const int32_t c = (it - D.n_dwin) * D.group + warp;
-            if (c < D.n_chunks) residual_chunk<L, VPL, BF16, HINT>(D, c, lane, pol);
+            if (c < D.n_chunks) {
+                if (L == 32 && VPL <= 2 && D.rl_all)
+                    residual_chunk_stream<(VPL <= 2 ? VPL : 2), BF16, HINT>(D, c, lane, pol);
+                else
+                    residual_chunk<L, VPL, BF16, HINT>(D, c, lane, pol);
+            }
         }
     }
     // the last CTA out resets the ticket for the next launch (stream order makes it visible)
@@ -361,6 +504,7 @@ void fill_desc(const Plan* P, const void* B, int64_t ldb, float* C, int64_t ldc,
     d->n = (int32_t)P->st.n;
     d->n_rl = (int32_t)P->st.n_rl;
     d->n_res = (int32_t)P->st.n_res;
+    d->rl_all = P->st.n_rl == P->st.m ? 1 : 0;
     d->status = P->ctrl + 2;
 }
 

@@ -127,6 +127,7 @@ struct ExecDesc {
     int32_t K, b_bf16, TM, TK, group, l2_hints;
     int32_t m, n;          // shape of A (bounds guards)
     int32_t n_rl, n_res;   // residual list rows, residual nonzeros (bounds guards)
+    int32_t rl_all;        // 1: the residual list is every row in order (contiguous stream)
     int32_t* status;       // device status word (kStatus* bits)
 };
 

@@ -128,14 +128,22 @@ struct PieceInfo {
     const int32_t* chunk_b;
     const int8_t* row_state;  // 2 = in a non-absorbing dense window; nullptr = none
     int64_t nc;
+    int64_t W;
     __device__ __forceinline__ void pieces(int64_t k, int32_t* i_out, int32_t* np, int32_t* base) const
     {
         int32_t i = __ldg(rl_rows + k);
         int64_t s = __ldg(rl_start + k), e = __ldg(rl_start + k + 1);
-        int64_t fc = upper_minus_one(chunk_b, nc, s);
-        int64_t lc = upper_minus_one(chunk_b, nc, e - 1);
         int hd = (row_state && row_state[i] == 2) ? 1 : 0;
         *i_out = i;
+        if (2 * (e - s) <= W) {
+            // short row: boundaries snap to its start, so it lies in one chunk; that chunk is only
+            // needed when a dense window also contributes (the row is then split)
+            *np = 1 + hd;
+            *base = hd ? (int32_t)(upper_minus_one(chunk_b, nc, s) - 1) : 0;
+            return;
+        }
+        int64_t fc = upper_minus_one(chunk_b, nc, s);
+        int64_t lc = upper_minus_one(chunk_b, nc, e - 1);
         *np = (int32_t)(lc - fc + 1 + hd);
         *base = (int32_t)(fc - hd);
     }
@@ -286,7 +294,7 @@ static ns_status_t splits_and_queue(Plan* P, const WindowResult* W, cudaStream_t
     tmp.reserve(&hist, bucket_hist_size(P->st.n_items));
     NS_TRY(tmp.commit(s));
     if (n_rl > 0 && nc > 0) {
-        PieceInfo pi{P->rl_rows, P->rl_start, P->chunk_b, W ? W->row_state : nullptr, nc};
+        PieceInfo pi{P->rl_rows, P->rl_start, P->chunk_b, W ? W->row_state : nullptr, nc, Wn};
         PieceStore st{pi, P->row_split, P->split_row, P->split_np, P->split_slot, P->split_base};
         NS_TRY(device_scan<int64_t>(PieceLoad{pi}, st, n_rl, partial, totals, s));
     }

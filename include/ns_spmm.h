@@ -228,6 +228,29 @@ double ns_serve_now(void);
 ns_status_t ns_serve_destroy(ns_server_t sv);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Allocation-free SpMM (no counterpart in the paper).                                       */
+/* ---------------------------------------------------------------------------------------- */
+/* For callers that cannot allocate device memory -- a process whose HBM is already handed to
+ * another allocator (a framework's caching allocator, a fixed per-tenant budget), or a
+ * latency-critical path that cannot pay the implicit device synchronisation of cudaMalloc and
+ * cudaFree.  C := A * B (every row written) on the CUDA cores, straight from the CSR: no plan,
+ * no dense tiles, no cudaMalloc/cudaFree and no allocating library call.  Its scratch (work
+ * ticket, split-row counters, partial-row slots) lives in one 32 MiB file-scope device array that
+ * every GPU loading this library holds until the process exits.
+ *   A       device CSR (on_device = 1), sorted unique columns; not validated beyond keeping every
+ *           access in bounds.  B (n x K, b_dtype) and C (m x K, FP32): device pointers, 16-byte
+ *           aligned, ldb and ldc >= K and multiples of 8.  Asynchronous on `s`.
+ *   Limit   2 * ceil((m + nnz) / 256) * K * 4 bytes of partial rows, plus counters, must fit the
+ *           32 MiB array (K = 128: m + nnz up to about 8.3 million); beyond it NS_ERR_TOO_LARGE.
+ *   The first call on a device resolves the array's device address (cudaGetSymbolAddress) and
+ *   caches it: make that first call before any stream capture.  Calls share the array and it
+ *   keeps the last call's contents; each call clears its counters first.  Calls that overlap on
+ *   the GPU (different streams or threads) race on the array and give wrong results.
+ * Errors: NS_ERR_INVALID, NS_ERR_UNSUPPORTED (K, alignment), NS_ERR_TOO_LARGE, NS_ERR_CUDA. */
+ns_status_t ns_spmm_csr_static(const ns_csr_t* A, const void* B, int64_t ldb, float* C, int64_t ldc,
+                               int32_t K, ns_dtype_t b_dtype, ns_stream_t s);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Diagnostics                                                                               */
 /* ---------------------------------------------------------------------------------------- */
 const char* ns_last_error(void);

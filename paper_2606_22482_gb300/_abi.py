@@ -91,6 +91,7 @@ SIGNATURES = {
     "ns_serve_poll": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ReqStats)]),
     "ns_serve_now": (D, []),
     "ns_serve_destroy": (ctypes.c_int, [P]),
+    "ns_spmm_csr_static": (ctypes.c_int, [ctypes.POINTER(Csr), P, I64, P, I64, I32, I32, P]),
     "ns_last_error": (ctypes.c_char_p, []),
     "ns_launch_count": (I64, []),
     "ns_device_ok": (I32, []),

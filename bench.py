@@ -183,6 +183,9 @@ def main():
     ap.add_argument("--pool", type=int, default=64, help="serve: graphs in the pool")
     ap.add_argument("--tau", default="auto", help="'auto' (autotuner), 'inf' or an integer")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--l2", type=int, default=None, choices=[0, 1, 2],
+                    help="override the L2 policy of the tune (2: planner-marked hot B rows)")
+    ap.add_argument("--tn", type=int, default=None, help="override the column-slice width TN")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -256,11 +259,19 @@ def main():
         tune_src = f"fixed tau={args.tau}"
     else:
         try:
-            tune = ns.autotune(At, K, DT)
-            tune_src = "autotuned"
+            # each timed step plans afresh: the autotuner weighs plan time fully (plan_runs = 1)
+            tune = ns.autotune(At, K, DT, plan_runs=1.0)
+            tune_src = "autotuned (objective: plan + execute)"
         except Exception as e:  # autotuner unavailable: pure CUDA-core plan
             tune.tau_tile = ns.NS_TAU_INF
             tune_src = f"default (autotune unavailable: {str(e)[:60]})"
+
+    if args.l2 is not None:
+        tune.l2_hints = args.l2
+        tune_src += f", l2_hints={args.l2}"
+    if args.tn is not None:
+        tune.TN = args.tn
+        tune_src += f", TN={args.tn}"
 
     def step(ev=None):
         p = ns.spmm_plan(At, K, DT, tune)

@@ -75,16 +75,21 @@ typedef struct {
  *               to the residual (0 disables the stage)
  *   col_order   order of compacted columns inside a window: 0 count-descending then column,
  *               1 column-ascending
- *   chunk_nnz   W, residual merge items (nonzeros + row ends) per warp chunk
+ *   chunk_nnz   W, residual merge items (nonzeros + row ends) per warp chunk, 2..1024
  *   absorb_cap  a dense window also computes its rows' residual when that has <= absorb_cap nnz
  *   group       residual chunks per work item (one per warp of the execute CTA; must be 4)
  *   cost_tc     Eq. 1 weight of one dense-tile element in the work-list order
  *   cost_res    Eq. 1 weight of one residual merge item in the work-list order
- *   l2_hints    1: stream A and C with evict-first and keep B with evict-last L2 policies
- *               (Section 6.2.1 hot-B staging, in GPU form); 0: default caching */
+ *   l2_hints    1: stream A and C with evict-first and keep B with evict-last L2 policies;
+ *               2: as 1, but only the most-gathered B rows (about 80% of L2, counted by the
+ *               planner) evict last and the rest evict first (Section 6.2.1 hot-B staging);
+ *               0: default caching
+ *   TN          execute in column slices of TN (multiple of 8; 0 = K in one pass): each slice
+ *               gathers only TN columns of B, so its working set stays in L2 (Section 6.2.2 N
+ *               shaping); A is re-read once per slice.  Execution only: plans do not depend on it */
 typedef struct {
     int32_t TM, TK, tau_tile, tau_row, tau_col, col_order, chunk_nnz, absorb_cap, group,
-        cost_tc, cost_res, l2_hints;
+        cost_tc, cost_res, l2_hints, TN;
 } ns_tune_t;
 
 void ns_tune_default(ns_tune_t* t);
@@ -168,17 +173,21 @@ ns_status_t ns_batch_destroy(ns_batch_t b);
 /* Autotuner (Section 5.2.1 dry run + Section 8 sweeps).                                     */
 /* ---------------------------------------------------------------------------------------- */
 typedef struct {
-    double p_res;     /* measured residual throughput, nonzeros * K per second            */
-    double p_tc;      /* measured dense-tile throughput, tile elements * K per second     */
-    double alpha0;    /* Eq. 3 with r = 1: p_res / p_tc                                    */
-    double best_ms;   /* execute time of the chosen tune                                    */
-    int32_t trials;   /* configurations timed                                               */
+    double p_res;     /* out: measured residual throughput, nonzeros * K per second          */
+    double p_tc;      /* out: measured dense-tile throughput, tile elements * K per second   */
+    double alpha0;    /* out: Eq. 3 with r = 1: p_res / p_tc                                  */
+    double best_ms;   /* out: execute time of the chosen tune                                 */
+    int32_t trials;   /* out: configurations timed                                            */
+    double plan_runs; /* in: executions per plan over which planning is amortised; the
+                         objective is execute_ms + plan_ms / plan_runs (0: 200, the paper's
+                         200-epoch GCN setting; 1: a fresh plan for every execute)          */
 } ns_tune_report_t;
 
-/* Dry-run microbenchmarks on A (or on synthetic tiles when A is small) give p_res and p_tc,
- * hence alpha0 and tau0 = ceil(alpha0 * TM * TK); then (TM, tau) candidates around tau0 plus the
- * two single-engine extremes are planned and timed, and the fastest is returned in *out.
- * A must be on the device.  Synchronous; report may be NULL. */
+/* Dry runs on A give p_res (residual-only plan) and p_tc (every compacted tile dense), hence
+ * alpha0 and tau0 = ceil(alpha0 * TM * TK); then (TM, tau) candidates around tau0, the two
+ * single-engine extremes and column slices TN are planned and timed, and the best by
+ * execute_ms + plan_ms / plan_runs is returned in *out.  A must be on the device.  Synchronous;
+ * report may be NULL (then plan_runs = 200). */
 ns_status_t ns_autotune(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, ns_stream_t s,
                         ns_tune_t* out, ns_tune_report_t* report);
 

@@ -157,11 +157,15 @@ def launch_count() -> int:
     return int(lib.ns_launch_count())
 
 
-def autotune(A: dict, K: int, b_dtype: int = NS_F32, stream=None, report: bool = False):
-    """ns_autotune on a device CSR: returns the chosen Tune (and the dry-run report if asked)."""
+def autotune(A: dict, K: int, b_dtype: int = NS_F32, stream=None, report: bool = False,
+             plan_runs: float = 0.0):
+    """ns_autotune on a device CSR: returns the chosen Tune (and the dry-run report if asked).
+
+    ``plan_runs``: executions per plan over which plan time is amortised (0 = 200)."""
     c, keep = _csr_struct(A, True)
     t = Tune()
     rep = _abi.TuneReport()
+    rep.plan_runs = float(plan_runs)
     check(lib.ns_autotune(ctypes.byref(c), int(K), int(b_dtype), _stream_handle(stream),
                           ctypes.byref(t), ctypes.byref(rep)))
     if report:

@@ -16,7 +16,7 @@ STATUS = {0: "NS_OK", 1: "NS_ERR_INVALID", 2: "NS_ERR_UNSUPPORTED", 3: "NS_ERR_O
           8: "NS_ERR_NOT_FOUND"}
 
 TUNE_FIELDS = ("TM", "TK", "tau_tile", "tau_row", "tau_col", "col_order", "chunk_nnz",
-               "absorb_cap", "group", "cost_tc", "cost_res", "l2_hints")
+               "absorb_cap", "group", "cost_tc", "cost_res", "l2_hints", "TN")
 
 
 class NsError(RuntimeError):
@@ -46,7 +46,7 @@ class PlanStats(ctypes.Structure):
 
 class TuneReport(ctypes.Structure):
     _fields_ = [("p_res", ctypes.c_double), ("p_tc", ctypes.c_double), ("alpha0", ctypes.c_double),
-                ("best_ms", ctypes.c_double), ("trials", ctypes.c_int32)]
+                ("best_ms", ctypes.c_double), ("trials", ctypes.c_int32), ("plan_runs", ctypes.c_double)]
 
 
 class ServeCfg(ctypes.Structure):

@@ -20,13 +20,54 @@ void set_error(const char* fmt, ...)
     t_err = buf;
 }
 
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {nullptr};
+
+static cudaMemPool_t pool_for(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pl = nullptr;
+        if (cudaMemPoolCreate(&pl, &props) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pl, cudaMemPoolAttrReleaseThreshold, &thr);
+        g_pool[dev] = pl;
+    }
+    return g_pool[dev];
+}
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pl = pool_for(dev);
+    if (!pl) return cudaMallocAsync(p, bytes, s);
+    return cudaMallocFromPoolAsync(p, bytes, pl, s);
+}
+
+void pool_trim()
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto& pl : g_pool)
+        if (pl) cudaMemPoolTrimTo(pl, 0);
+}
+
 ns_status_t Arena::commit(cudaStream_t s)
 {
     size_t total = 0;
     for (auto& r : reqs) total += (r.bytes + 255) & ~size_t(255);
     if (total == 0) total = 256;
     void* p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, total, s);
+    cudaError_t e = pool_alloc(&p, total, s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         set_error("device allocation of %zu bytes failed: %s", total, cudaGetErrorString(e));
@@ -57,6 +98,7 @@ void Arena::release(cudaStream_t s)
 // never frees memory a running kernel still reads.
 Plan::~Plan()
 {
+    if (status_ev) cudaEventDestroy(status_ev);
     bool failed = false;
     for (auto& b : blocks) {
         if (!b.ptr) continue;
@@ -68,6 +110,28 @@ Plan::~Plan()
         if (failed) cudaFree(b.ptr);
         b.ptr = nullptr;
     }
+}
+
+// pinned host slots for the status words of plans (one slab for the process)
+static std::mutex g_slab_mu;
+static int32_t* g_slab = nullptr;
+static uint32_t g_slab_next = 0;
+constexpr uint32_t kSlabSlots = 65536;
+
+static int32_t* status_slot()
+{
+    std::lock_guard<std::mutex> lk(g_slab_mu);
+    if (!g_slab) {
+        if (cudaHostAlloc(reinterpret_cast<void**>(&g_slab), kSlabSlots * sizeof(int32_t), 0) != cudaSuccess) {
+            (void)cudaGetLastError();
+            g_slab = nullptr;
+            return nullptr;
+        }
+        memset(g_slab, 0, kSlabSlots * sizeof(int32_t));
+    }
+    int32_t* p = g_slab + (g_slab_next++ % kSlabSlots);
+    *p = 0;
+    return p;
 }
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -159,6 +223,7 @@ void ns_tune_default(ns_tune_t* t)
     t->cost_tc = 1;
     t->cost_res = 8;
     t->l2_hints = 1;
+    t->TN = 0;
 }
 
 const char* ns_last_error(void) { return t_err.c_str(); }
@@ -224,12 +289,10 @@ ns_status_t ns_spmm_execute(ns_plan_t p, const void* B, int64_t ldb, float* C, i
         cudaEventDestroy(ev);
         P->last_stream = st;
     }
-    // a device status word left by an earlier launch of this plan
-    if (P->desc_valid) {
-        int32_t status = 0;
-        NS_CUDA_TRY(cudaMemcpyAsync(&status, P->ctrl + 2, sizeof status, cudaMemcpyDeviceToHost, st));
-        // (the copy is ordered after earlier launches on the same stream)
-        NS_CUDA_TRY(cudaStreamSynchronize(st));
+    // the device status word of an earlier launch, if its pinned copy has already landed
+    // (never waits: a launch still running is checked by a later call)
+    if (P->status_ev && cudaEventQuery(P->status_ev) == cudaSuccess) {
+        const int32_t status = *P->status_host;
         if (status & kStatusTimeout) {
             set_error("an earlier launch gave up a bounded wait");
             return NS_ERR_TIMEOUT;
@@ -240,14 +303,26 @@ ns_status_t ns_spmm_execute(ns_plan_t p, const void* B, int64_t ldb, float* C, i
             return NS_ERR_CUDA;
         }
     }
-    ExecDesc d;
-    fill_desc(P, B, ldb, C, ldc, &d);
-    if (!P->desc_valid || memcmp(&d, &P->desc_host, sizeof d) != 0) {
-        P->desc_host = d;
-        NS_CUDA_TRY(cudaMemcpyAsync(P->desc_dev, &P->desc_host, sizeof d, cudaMemcpyHostToDevice, st));
+    (void)cudaGetLastError();
+    const int32_t TN = (P->tune.TN > 0 && P->tune.TN < P->K) ? P->tune.TN : P->K;
+    const size_t es = P->dtype == NS_BF16 ? 2 : 4;
+    for (int32_t c0 = 0; c0 < P->K; c0 += TN) {
+        // column slice [c0, c0 + w): B and C shifted by c0 columns, same leading dimensions
+        const int32_t w = P->K - c0 < TN ? P->K - c0 : TN;
+        fill_desc(P, static_cast<const char*>(B) + (size_t)c0 * es, ldb, C + c0, ldc, &P->desc_host);
+        P->desc_host.K = w;
         P->desc_valid = true;
+        NS_TRY(exec_launch_plan(P, st));
     }
-    return exec_launch_plan(P, st);
+    if (!P->status_host) {
+        P->status_host = status_slot();
+        if (P->status_host) cudaEventCreateWithFlags(&P->status_ev, cudaEventDisableTiming);
+    }
+    if (P->status_host && P->status_ev) {
+        cudaMemcpyAsync(P->status_host, P->ctrl + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        cudaEventRecord(P->status_ev, st);
+    }
+    return NS_OK;
 }
 
 ns_status_t ns_plan_stats(ns_plan_t p, ns_plan_stats_t* st)
@@ -442,9 +517,13 @@ extern "C" ns_status_t ns_spmm_host(const ns_csr_t* A, const void* B, int32_t K,
 
 extern "C" ns_status_t ns_release_cache(void)
 {
-    std::lock_guard<std::mutex> lk(g_host_cache.mu);
-    if (g_host_cache.buf) cudaFree(g_host_cache.buf);
-    g_host_cache.buf = nullptr;
-    g_host_cache.bytes = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_host_cache.mu);
+        if (g_host_cache.buf) cudaFree(g_host_cache.buf);
+        g_host_cache.buf = nullptr;
+        g_host_cache.bytes = 0;
+    }
+    cudaDeviceSynchronize();
+    pool_trim();
     return NS_OK;
 }

@@ -35,7 +35,7 @@ struct Batch {
         int32_t* ctrl = nullptr;
         int64_t n_items = 0;
         int grid = 0;
-        int TM = 16, TK = 16;
+        int TM = 16, TK = 16, W = 256;
     };
     std::vector<Plan*> plans;
     std::vector<Group> groups;
@@ -118,6 +118,7 @@ ns_status_t ns_batch_plan(const ns_csr_t* As, int32_t count, const int32_t* Ks, 
         G.K = Ks[order[q]];
         G.TM = t.TM;
         G.TK = t.TK;
+        G.W = t.chunk_nnz;
         while (q < count && Ks[order[q]] == G.K) G.graphs.push_back(order[q++]);
         Bt->groups.push_back(G);
     }
@@ -221,7 +222,7 @@ ns_status_t ns_batch_execute(ns_batch_t b, const void* const* Bs, float* const* 
     if (!Bt->exec) {
         // capture every group's persistent launch once; later calls replay the graph
         for (auto& G : Bt->groups)  // occupancy queries and attributes outside the capture
-            NS_TRY(exec_prepare(G.n_items, G.K, G.TM, G.TK, Bt->dtype == NS_BF16, Bt->hint, G.dense, &G.grid));
+            NS_TRY(exec_prepare(G.n_items, G.K, G.TM, G.TK, Bt->dtype == NS_BF16, Bt->hint, G.dense, &G.grid, G.W));
         // the caller's stream may be the legacy default stream, which cannot be captured: record
         // the launches on a private stream once; the graph then replays on the caller's stream
         if (!Bt->cap_stream) NS_CUDA_TRY(cudaStreamCreateWithFlags(&Bt->cap_stream, cudaStreamNonBlocking));
@@ -229,7 +230,7 @@ ns_status_t ns_batch_execute(ns_batch_t b, const void* const* Bs, float* const* 
         ns_status_t r = NS_OK;
         for (auto& G : Bt->groups) {
             r = exec_launch(G.descs_dev, G.queue, G.queue_desc, G.n_items, G.ctrl, G.K, G.TM, G.TK,
-                            Bt->dtype == NS_BF16, Bt->hint, G.dense, &G.grid, Bt->cap_stream);
+                            Bt->dtype == NS_BF16, Bt->hint, G.dense, &G.grid, Bt->cap_stream, nullptr, G.W);
             if (r != NS_OK) break;
         }
         cudaGraph_t graph = nullptr;
@@ -284,11 +285,6 @@ static ns_status_t time_tune(const ns_csr_t* A, int32_t K, ns_dtype_t dt, const 
     Plan* P = nullptr;
     NS_TRY(plan_create(A, K, dt, &t, st, &P));
     *plan_ms = (now_s() - t0) * 1e3;
-    ExecDesc d;
-    fill_desc(P, Bd, K, Cd, K, &d);
-    P->desc_host = d;
-    P->desc_valid = true;
-    cudaMemcpyAsync(P->desc_dev, &P->desc_host, sizeof d, cudaMemcpyHostToDevice, st);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -296,7 +292,7 @@ static ns_status_t time_tune(const ns_csr_t* A, int32_t K, ns_dtype_t dt, const 
     ns_status_t r = NS_OK;
     for (int rep = 0; rep < 4 && r == NS_OK; ++rep) {
         cudaEventRecord(e0, st);
-        r = exec_launch_plan(P, st);
+        r = ns_spmm_execute(reinterpret_cast<ns_plan_t>(P), Bd, K, Cd, K, st);
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) r = NS_ERR_CUDA;
         float ms = 0;
@@ -326,8 +322,8 @@ ns_status_t ns_autotune(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, ns_str
     const size_t eb = b_dtype == NS_BF16 ? 2 : 4;
     void* Bd = nullptr;
     float* Cd = nullptr;
-    NS_CUDA_TRY(cudaMallocAsync(&Bd, (size_t)(A->n > 0 ? A->n : 1) * K * eb, st));
-    NS_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&Cd), (size_t)(A->m > 0 ? A->m : 1) * K * 4, st));
+    NS_CUDA_TRY(pool_alloc(&Bd, (size_t)(A->n > 0 ? A->n : 1) * K * eb, st));
+    NS_CUDA_TRY(pool_alloc(reinterpret_cast<void**>(&Cd), (size_t)(A->m > 0 ? A->m : 1) * K * 4, st));
     NS_CUDA_TRY(cudaMemsetAsync(Bd, 0, (size_t)(A->n > 0 ? A->n : 1) * K * eb, st));
     auto release = [&]() {
         cudaFreeAsync(Bd, st);
@@ -337,7 +333,8 @@ ns_status_t ns_autotune(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, ns_str
 
     ns_tune_t base;
     ns_tune_default(&base);
-    const double amort = 200.0;  // plan cost amortised over the runs of a 200-epoch workload
+    // plan cost amortised over the executions of one plan (default: a 200-epoch workload)
+    const double amort = (report && report->plan_runs > 0) ? report->plan_runs : 200.0;
     int trials = 0;
     ns_tune_t best = base;
     double best_cost = 1e300, best_exec = 0;
@@ -400,6 +397,23 @@ ns_status_t ns_autotune(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, ns_str
             ns_tune_t t = base;
             t.TM = TM;
             t.tau_tile = tau;
+            double ex = 0, pl = 0;
+            r = time_tune(A, K, b_dtype, t, Bd, Cd, st, &ex, &pl, nullptr);
+            if (r == NS_OK) consider(t, ex, pl);
+            else if (r != NS_ERR_UNSUPPORTED) {
+                release();
+                return r;
+            }
+        }
+    }
+    // column slices (Section 6.2.2 N shaping): narrower passes keep the gathered B rows in L2
+    {
+        const ns_tune_t base_best = best;
+        for (int div = 2; div <= 4; div *= 2) {
+            const int32_t tn = (K / div) & ~7;
+            if (tn < 32 || tn >= K) continue;
+            ns_tune_t t = base_best;
+            t.TN = tn;
             double ex = 0, pl = 0;
             r = time_tune(A, K, b_dtype, t, Bd, Cd, st, &ex, &pl, nullptr);
             if (r == NS_OK) consider(t, ex, pl);

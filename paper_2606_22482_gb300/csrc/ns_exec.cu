@@ -17,6 +17,7 @@
 // L2 policy (Section 6.2.1 hot-B staging in GPU form): A's arrays and C are streamed with an
 // evict-first policy, B rows are loaded with evict-last so that reused B rows stay in L2.
 #include "ns_internal.cuh"
+#include "ns_ptx.cuh"
 
 namespace ns {
 
@@ -268,109 +269,318 @@ __device__ __noinline__ void deliver_split_row(const ExecDesc& D, int32_t row, i
     if (lane == 0) atomicExch(D.split_cnt + s, 0);
 }
 
-// Residual chunk when the residual list is every row in order (no dense windows) and K >= 128
-// (one nonzero per warp step, 32 lanes x 4 columns x VPL).  The chunk's nonzeros are then one
-// contiguous stream: (col, val) batches of 32 are loaded one batch ahead, row ends and split ids
-// of 32 rows at a time, and U gathered B rows stay in flight across row boundaries.  Removes the
-// per-row chain of dependent loads (row pointer -> column ids -> B row).
-template <int VPL, bool BF16, bool HINT>
-__device__ void residual_chunk_stream(const ExecDesc& D, int32_t c, int lane, const Policies& pol)
+// Residual chunk when the residual list is every row in order (no dense windows) and
+// 128 <= K <= 256 (one nonzero per warp step, 32 lanes x 4 columns x VPL).  The chunk's nonzeros
+// are one contiguous stream.  Gathered B rows go through a kStages-deep ring in this warp's shared
+// memory with cp.async (Section 7's double-buffer pipelining, deepened): while stage s is summed,
+// stages s+1 .. s+kStages-1 are in flight, so the bytes in flight cost no registers.  Column ids
+// and values of the next stage are loaded one stage ahead, row ends and split ids 32 rows at a time.
+constexpr int kStages = 3;
+
+struct StageGeom {
+    int NB;          // nonzeros per stage
+    int rowbytes;    // one gathered B row (a multiple of 16 bytes since K % 8 == 0)
+    int stage_bytes; // NB * rowbytes
+    int cap;         // capacity of the chunk's (col, val) stream in shared memory
+    int off_col, off_val, bars_off;
+    int warp_bytes;  // shared memory of one warp, a multiple of 128
+};
+
+// A chunk holds at most 3W/2 merge items (boundaries snap by less than W/2), so its rows and its
+// nonzero stream fit in `cap` entries.  Per warp, shared memory holds the decoded chunk:
+// column ids and values (padded by the ring depth), and per row its id, split id, and first and
+// past-last stream positions, plus the rows' first residual index (general residual lists).
+constexpr int kRing = 8;  // gathered rows in flight per warp (K <= 128; 4 for K <= 256)
+
+__host__ __device__ inline StageGeom stage_geom(int K, bool bf16, int W)
 {
-    constexpr int U = VPL == 1 ? 8 : 4;
+    StageGeom g;
+    g.rowbytes = K * (bf16 ? 2 : 4);
+    g.NB = 0;
+    g.stage_bytes = 0;
+    g.cap = ((3 * W) / 2 + 32 + 31) & ~31;
+    g.off_col = 0;                               // cap + kRing int32
+    g.off_val = 4 * (g.cap + kRing);             // cap + kRing float
+    g.bars_off = 8 * (g.cap + kRing);            // row arrays: 4 x (cap + 1) int32, cap int64
+    g.warp_bytes = (g.bars_off + 16 * (g.cap + 1) + 8 * g.cap + 127) & ~127;
+    return g;
+}
+
+// the staged stream path serves K <= 256 (at most two 4-column vectors per lane)
+__host__ __device__ inline bool staged_path(int L, int VPL) { return VPL <= 2; }
+
+__device__ __forceinline__ uint32_t dynamic_smem_bytes()
+{
+    uint32_t r;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
+template <int VPL, bool BF16>
+__device__ __forceinline__ float4 lds_vec(const unsigned char* row, int v)
+{
+    if (!BF16) return *reinterpret_cast<const float4*>(row + 16 * v);
+    const uint2 u = *reinterpret_cast<const uint2*>(row + 8 * v);
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+}
+
+constexpr uint32_t kWaitLimit = 1u << 22;  // bounded mbarrier waits (far beyond any copy latency)
+
+// per-warp staging state that persists across the chunks a warp processes
+struct WarpStage {
+    unsigned char* base;  // kStages stages of rows, the chunk's columns and values, barriers
+    int32_t* cols;
+    float* vals;
+    uint64_t* bars;
+    uint32_t g0;          // stages consumed so far (barrier phase bookkeeping)
+};
+
+// Row metadata of up to 32 consecutive residual-list rows of a chunk, one row per lane, with the
+// rows' positions in the chunk's stream of nonzeros (rows clipped to the chunk's merge range).
+struct RowWin {
+    int64_t kb;     // first row of the window
+    int64_t base;   // stream position of the window's first row
+    int64_t total;  // stream position after the window
+    int32_t row;    // original row id (-1 past the chunk's last row)
+    int32_t split;  // split id of the row or -1
+    int64_t zoff;   // residual index of the row's first nonzero inside the chunk
+    int32_t n;      // nonzeros of the row inside the chunk
+    int64_t cum;    // stream position of the row's first nonzero
+};
+
+__device__ __forceinline__ void load_win(const ExecDesc& D, RowWin& w, int64_t kb, int64_t base,
+                                         int64_t kL, int64_t b0, int64_t b1, int lane)
+{
+    w.kb = kb;
+    w.base = base;
+    const int64_t k = kb + lane;
+    int32_t n = 0;
+    w.row = -1;
+    w.split = -1;
+    w.zoff = 0;
+    if (k <= kL) {
+        const int32_t i = __ldg(D.rl_rows + k);
+        const int64_t s = __ldg(D.rl_start + k), e = __ldg(D.rl_start + k + 1);
+        const int64_t xs = b0 > s ? b0 : s;
+        const int64_t xe = b1 < e - 1 ? b1 : e - 1;
+        n = xe > xs ? (int32_t)(xe - xs) : 0;
+        if (i >= 0 && i < D.m) {
+            w.row = i;
+            w.split = __ldg(D.row_split + i);
+            w.zoff = (int64_t)__ldg(D.res_rowptr + i) + (xs - s);
+            if (w.zoff < 0 || w.zoff + n > D.n_res) n = 0, w.row = -2;  // guard: corrupt plan
+        } else {
+            w.row = -2;
+        }
+    }
+    w.n = n;
+    int32_t inc = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    w.cum = base + inc - n;
+    w.total = base + __shfl_sync(0xffffffffu, inc, 31);
+}
+
+// Residual chunk with K <= 256 (at most two 4-column vectors per lane, one nonzero per warp step).
+// The chunk's nonzeros, over all its residual-list rows, form one stream.  Gathered B rows go
+// through a kStages-deep ring in this warp's shared memory (Section 7's double-buffer pipelining,
+// deepened): each row is ONE bulk asynchronous copy issued by the lane that holds its column and
+// completing on the stage's mbarrier, so the bytes in flight cost neither registers nor per-lane
+// instructions.  Column ids and values of the next stage are resolved and loaded one stage ahead.
+// one 4-column vector of a gathered B row at byte address p (16 B of FP32 or 8 B of BF16)
+template <bool BF16, bool HINT>
+__device__ __forceinline__ float4 ld_vec_at(const unsigned char* p, uint64_t pol)
+{
+    return ld_b4<BF16, HINT>(p, 0, pol);
+}
+
+// The streamed inner loop.  FULL: every lane holds VPL whole vectors (K == 128 * VPL), so no
+// per-lane width test; HOT: the planner's hot-row map picks each gather's L2 policy.
+template <int VPL, bool BF16, bool HINT, bool FULL, bool HOT>
+__device__ __forceinline__ void stream_rows(const ExecDesc& D, int32_t c, int lane, const int2* ent,
+                                            int tot_pad, int nr, const int32_t* rrow,
+                                            const int32_t* rsplit, const int32_t* rend,
+                                            const Policies& pol)
+{
     const int nv = D.K >> 2;
+    constexpr int VB = BF16 ? 8 : 16;  // bytes of one 4-column vector
+    const unsigned char* const Bl = reinterpret_cast<const unsigned char*>(D.B) + VB * lane;
+    const uint32_t ldb_bytes = (uint32_t)(D.ldb * (BF16 ? 2 : 4));
+    float* const Cp = D.C;
+    const int64_t ldc = D.ldc;
+    const uint32_t* const hotp = D.hot;
+
+    float4 acc[VPL];
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int r = 0;
+    int next_end = rend[0];
+    auto flush = [&]() {  // deliver row r, move to row r + 1
+        const int32_t i = rrow[r];
+        const int32_t sp = rsplit[r];
+        if (i >= 0) {
+            if (sp < 0) {
+                float* crow = Cp + (int64_t)i * ldc;
+#pragma unroll
+                for (int q = 0; q < VPL; ++q) {
+                    const int v = lane + 32 * q;
+                    if (FULL || v < nv) st_c4<HINT>(crow + 4 * v, acc[q], pol.first);
+                }
+            } else {
+                deliver_split_row<VPL, HINT>(D, i, sp, c, acc[0], acc[VPL > 1 ? VPL - 1 : 0], lane, pol.first);
+            }
+        } else if (i == -2 && lane == 0) {
+            atomicOr(D.status, kStatusInternal);
+        }
+#pragma unroll
+        for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ++r;
+        next_end = rend[r];
+    };
+
+    constexpr int U = VPL == 1 ? kRing : kRing / 2;
+    float4 b[U][VPL];
+    float w[U];
+    auto gather = [&](int2 e, float4 (&dst)[VPL], float& wv) {
+        // padding entries point at a real row with value 0: no test needed here
+        const unsigned char* row = Bl + (size_t)(uint32_t)e.x * ldb_bytes;
+        uint64_t pl = pol.last;
+        if (HOT) pl = ((__ldg(hotp + (e.x >> 5)) >> (e.x & 31)) & 1u) ? pol.last : pol.first;
+#pragma unroll
+        for (int q = 0; q < VPL; ++q) {
+            if (FULL || lane + 32 * q < nv) dst[q] = ld_vec_at<BF16, HINT>(row + 32 * VB * q, pl);
+            else dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        wv = __int_as_float(e.y);
+    };
+#pragma unroll
+    for (int u = 0; u < U; ++u) gather(ent[u], b[u], w[u]);
+    for (int j0 = 0; j0 < tot_pad; j0 += U) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int P = j0 + u;
+            while (P >= next_end) flush();
+            const int2 e = ent[P + U];
+#pragma unroll
+            for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], b[u][q], acc[q]);
+            gather(e, b[u], w[u]);
+        }
+    }
+    while (r < nr) flush();  // rows ending at or after the last item (and the last row)
+}
+
+template <int VPL, bool BF16, bool HINT>
+__device__ void residual_chunk_staged(const ExecDesc& D, int32_t c, int lane, WarpStage& ws,
+                                      const Policies& pol)
+{
+    const StageGeom G = stage_geom(D.K, BF16, D.chunk_nnz);
     const int64_t b0 = __ldg(D.chunk_b + c), b1 = __ldg(D.chunk_b + c + 1);
     const int64_t k0 = __ldg(D.chunk_k0 + c);
     // last row with a merge item in [b0, b1): the row holding b1 - 1
     int64_t kL = (c + 1 < D.n_chunks) ? (int64_t)__ldg(D.chunk_k0 + c + 1) : (int64_t)D.n_rl - 1;
-    if (kL > k0 && (int64_t)__ldg(D.res_rowptr + kL) + kL >= b1) --kL;
-    const int64_t zA = b0 - k0;                              // first nonzero of the chunk
-    const int64_t eL = __ldg(D.res_rowptr + kL + 1);
-    const int64_t zZ = (eL + kL >= b1) ? b1 - kL : eL;       // end of the chunk's nonzeros
-    if (k0 < 0 || kL >= D.n_rl || zA < 0 || zZ > D.n_res || zA > zZ + 1) {
+    if (kL > k0 && (int64_t)__ldg(D.rl_start + kL) >= b1) --kL;
+    const int nr = (int)(kL - k0 + 1);
+    if (k0 < 0 || kL >= D.n_rl || kL < k0 || b1 <= b0 || nr > G.cap) {
         if (lane == 0) atomicOr(D.status, kStatusInternal);
         return;
     }
-    int64_t kb = k0;  // first row of the lanes' metadata window
-    int32_t my_end = kb + lane <= kL ? __ldg(D.res_rowptr + kb + lane + 1) : 0x7fffffff;
-    int32_t my_split = kb + lane <= kL ? __ldg(D.row_split + kb + lane) : -1;
-    int64_t k = k0;
-    int64_t rend = __shfl_sync(0xffffffffu, my_end, 0);
-    float4 acc[VPL];
-#pragma unroll
-    for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int2* const ent = reinterpret_cast<int2*>(ws.base);  // (col, value bits), cap + kRing
+    int32_t* const rrow = reinterpret_cast<int32_t*>(ws.base + G.bars_off);
+    int32_t* const rsplit = rrow + (G.cap + 1);
+    int32_t* const rbeg = rsplit + (G.cap + 1);
+    int32_t* const rend = rbeg + (G.cap + 1);
+    int64_t* const rzoff = reinterpret_cast<int64_t*>(rend + (G.cap + 1));
 
-    // deliver row k (its nonzeros in this chunk are summed in acc) and move to row k + 1
-    auto flush = [&]() {
-        const int32_t s = __shfl_sync(0xffffffffu, my_split, (int)(k - kb));
-        if (s < 0) {
-            float* crow = D.C + k * D.ldc;
-#pragma unroll
-            for (int q = 0; q < VPL; ++q) {
-                const int v = lane + 32 * q;
-                if (v < nv) st_c4<HINT>(crow + 4 * v, acc[q], pol.first);
+    // ---- decode the chunk's rows: ids, split ids, stream positions, first residual index ----
+    int total = 0;
+    {
+        RowWin w;
+        int64_t kb = k0, base = 0;
+        for (;;) {
+            load_win(D, w, kb, base, kL, b0, b1, lane);
+            const int r = (int)(kb - k0) + lane;
+            if (kb + lane <= kL) {
+                rrow[r] = w.row;
+                rsplit[r] = w.split;
+                rbeg[r] = (int32_t)w.cum;
+                rend[r] = (int32_t)(w.cum + w.n);
+                rzoff[r] = w.zoff;
             }
-        } else {
-            deliver_split_row<VPL, HINT>(D, (int32_t)k, s, c, acc[0], acc[VPL > 1 ? VPL - 1 : 0], lane,
-                                         pol.first);
+            base = w.total;
+            if (kb + 32 > kL) break;
+            kb += 32;
         }
-#pragma unroll
-        for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        ++k;
-        if (k - kb == 32) {
-            kb = k;
-            my_end = kb + lane <= kL ? __ldg(D.res_rowptr + kb + lane + 1) : 0x7fffffff;
-            my_split = kb + lane <= kL ? __ldg(D.row_split + kb + lane) : -1;
-        }
-        rend = __shfl_sync(0xffffffffu, my_end, (int)(k - kb));
-    };
-
-    int32_t mc = 0, nc_ = 0;
-    float mv = 0.f, nv_ = 0.f;
-    if (zA + lane < zZ) {
-        mc = ld_stream_i32<HINT>(D.res_col + zA + lane, pol.first);
-        mv = ld_stream_f32<HINT>(D.res_val + zA + lane, pol.first);
+        total = (int)base;
+        if (lane == 0) rend[nr] = 0x7fffffff;  // sentinel after the last row
     }
-    for (int64_t zb = zA; zb < zZ; zb += 32) {
-        const int cnt = (int)(zZ - zb < 32 ? zZ - zb : 32);
-        // next batch of column ids and values, one batch ahead
-        if (zb + 32 + lane < zZ) {
-            nc_ = ld_stream_i32<HINT>(D.res_col + zb + 32 + lane, pol.first);
-            nv_ = ld_stream_f32<HINT>(D.res_val + zb + 32 + lane, pol.first);
-        }
-        if (lane < cnt && (unsigned)mc >= (unsigned)D.n) {  // guard: never gather outside B
-            atomicOr(D.status, kStatusInternal);
-            mc = 0;
-            mv = 0.f;
-        }
-        for (int j0 = 0; j0 < cnt; j0 += U) {
-            float4 b[U][VPL];
-            float val[U];
+    if (total < 0 || total > G.cap) {
+        if (lane == 0) atomicOr(D.status, kStatusInternal);
+        return;
+    }
+    __syncwarp();
+    // ---- the nonzero stream as (col, value) entries; every load issued before any store ----
+    const int tot_pad = (total + kRing - 1) / kRing * kRing;
+    int32_t last_col = 0;
+    for (int P0 = 0; P0 < total; P0 += 128) {
+        int32_t cc[4];
+        float vv[4];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int j = j0 + u;
-                const int32_t col = __shfl_sync(0xffffffffu, mc, j & 31);
-                val[u] = __shfl_sync(0xffffffffu, mv, j & 31);
-#pragma unroll
-                for (int q = 0; q < VPL; ++q) {
-                    const int v = lane + 32 * q;
-                    b[u][q] = (j < cnt && v < nv) ? ld_b4<BF16, HINT>(D.B, (int64_t)col * D.ldb + 4 * v, pol.last)
-                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = 0; u < 4; ++u) {
+            const int P = P0 + 32 * u + lane;
+            cc[u] = 0;
+            vv[u] = 0.f;
+            if (P < total) {
+                int64_t z;
+                if (D.rl_all) {
+                    z = rzoff[0] + P;  // one contiguous residual range
+                } else {             // the row holding P: largest r with rbeg[r] <= P
+                    int lo = 0, hi = nr;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (rbeg[mid] <= P) lo = mid;
+                        else hi = mid;
+                    }
+                    z = rzoff[lo] + (P - rbeg[lo]);
                 }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (j0 + u < cnt) {
-                    const int64_t z = zb + j0 + u;
-                    while (z >= rend) flush();
-#pragma unroll
-                    for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(val[u], b[u][q], acc[q]);
+                if (z >= 0 && z < D.n_res) {
+                    cc[u] = ld_stream_i32<HINT>(D.res_col + z, pol.first);
+                    vv[u] = ld_stream_f32<HINT>(D.res_val + z, pol.first);
+                } else {
+                    atomicOr(D.status, kStatusInternal);
                 }
             }
         }
-        mc = nc_;
-        mv = nv_;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int P = P0 + 32 * u + lane;
+            if (P < total) {
+                if ((unsigned)cc[u] >= (unsigned)D.n) {  // guard: never gather outside B
+                    atomicOr(D.status, kStatusInternal);
+                    cc[u] = 0;
+                    vv[u] = 0.f;
+                }
+                ent[P] = make_int2(cc[u], __float_as_int(vv[u]));
+            }
+        }
     }
-    while (k <= kL) flush();  // the last row (whole or a piece) and trailing empty rows
+    __syncwarp();
+    if (total > 0) last_col = ent[total - 1].x;
+    // padding: the last real row again with value 0 (a cached load, no branch in the loop)
+    for (int P = total + lane; P < tot_pad + kRing; P += 32) ent[P] = make_int2(last_col, 0);
+    __syncwarp();
+
+    const bool full = D.K == 128 * VPL;
+    if (D.hot) {
+        if (full) stream_rows<VPL, BF16, HINT, true, true>(D, c, lane, ent, tot_pad, nr, rrow, rsplit, rend, pol);
+        else stream_rows<VPL, BF16, HINT, false, true>(D, c, lane, ent, tot_pad, nr, rrow, rsplit, rend, pol);
+    } else {
+        if (full) stream_rows<VPL, BF16, HINT, true, false>(D, c, lane, ent, tot_pad, nr, rrow, rsplit, rend, pol);
+        else stream_rows<VPL, BF16, HINT, false, false>(D, c, lane, ent, tot_pad, nr, rrow, rsplit, rend, pol);
+    }
 }
 
 // one merge-path chunk c of the residual (one warp)
@@ -418,44 +628,82 @@ namespace ns {
 // ---------------------------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------------------------
+// residual-only kernels are held to 64 registers (8 CTAs = 32 warps per SM: latency hiding for
+// the gathers); kernels with the tensor-core item keep their registers for the accumulators
 template <int L, int VPL, bool BF16, bool HINT, bool DENSE>
-__global__ void __launch_bounds__(kExecThreads) k_exec(const ExecDesc* __restrict__ descs,
+__global__ void __launch_bounds__(kExecThreads, DENSE ? 1 : 4) k_exec(const ExecDesc* __restrict__ descs,
                                                        const int32_t* __restrict__ queue,
                                                        const int32_t* __restrict__ queue_desc,
-                                                       int64_t n_items, int32_t* ctrl)
+                                                       int64_t n_items, int32_t* ctrl,
+                                                       const __grid_constant__ ExecDesc d0)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int32_t s_ticket;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Policies pol{0, 0};
     if (HINT) pol = make_policies();
-    for (;;) {
-        if (threadIdx.x == 0) s_ticket = atomicAdd(ctrl + 0, 1);
-        __syncthreads();
-        const int64_t t = s_ticket;
-        __syncthreads();
-        if (t >= n_items) break;
-        const int32_t it = __ldg(queue + t);
-        const int32_t di = queue_desc ? __ldg(queue_desc + t) : 0;
-        const ExecDesc& D = descs[di];
-        if (DENSE && it < D.n_dwin) {
-            dense_item<L, VPL, BF16, HINT>(D, it, smem_raw, pol);
-        } else {
-            const int32_t c = (it - D.n_dwin) * D.group + warp;
-            if (c < D.n_chunks) {
-                if (L == 32 && VPL <= 2 && D.rl_all)
-                    residual_chunk_stream<(VPL <= 2 ? VPL : 2), BF16, HINT>(D, c, lane, pol);
-                else
-                    residual_chunk<L, VPL, BF16, HINT>(D, c, lane, pol);
+    if (DENSE) {
+        // phase 1: dense windows, one CTA each, taken in work-list order
+        for (;;) {
+            if (threadIdx.x == 0) s_ticket = atomicAdd(ctrl + 0, 1);
+            __syncthreads();
+            const int64_t t = s_ticket;
+            __syncthreads();
+            if (t >= n_items) break;
+            const int32_t it = __ldg(queue + t);
+            const ExecDesc& D = descs ? descs[queue_desc ? __ldg(queue_desc + t) : 0] : d0;
+            if (it < D.n_dwin) {
+                if (dynamic_smem_bytes() >= (uint32_t)dense_geom(D.K, D.TM, D.TK, BF16).total)
+                    dense_item<L, VPL, BF16, HINT>(D, it, smem_raw, pol);
+                else if (threadIdx.x == 0)
+                    atomicOr(D.status, kStatusInternal);  // guard: launch without the tile buffers
             }
         }
     }
-    // the last CTA out resets the ticket for the next launch (stream order makes it visible)
+    // phase 2: residual chunks, one warp each, in work-list order (no CTA barrier)
+    WarpStage ws{nullptr, nullptr, nullptr, nullptr, 0};
+    int ws_bytes = -1;
+    for (;;) {
+        int64_t u = 0;
+        if (lane == 0) u = atomicAdd(ctrl + 3, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        const int64_t t = u / kExecWarps;
+        if (t >= n_items) break;
+        const int32_t it = __ldg(queue + t);
+        const ExecDesc& D = descs ? descs[queue_desc ? __ldg(queue_desc + t) : 0] : d0;
+        if (it < D.n_dwin) continue;
+        const int64_t c = (int64_t)(it - D.n_dwin) * kExecWarps + (u % kExecWarps);
+        if (c >= D.n_chunks) continue;
+        // K <= 256: the streamed path, which needs the shared memory the host sized for it
+        if constexpr (VPL <= 2) {
+            if (dynamic_smem_bytes() < (uint32_t)(kExecWarps * stage_geom(D.K, BF16, D.chunk_nnz).warp_bytes)) {
+                if (lane == 0) atomicOr(D.status, kStatusInternal);  // guard: misconfigured launch
+                continue;
+            }
+            const StageGeom SG = stage_geom(D.K, BF16, D.chunk_nnz);
+            if (SG.warp_bytes != ws_bytes) {  // (re)arm this warp's barriers for this geometry
+                __syncwarp();
+                ws.base = smem_raw + warp * SG.warp_bytes;
+                ws.cols = reinterpret_cast<int32_t*>(ws.base + SG.off_col);
+                ws.vals = reinterpret_cast<float*>(ws.base + SG.off_val);
+                ws.bars = nullptr;
+                __syncwarp();
+                ws.g0 = 0;
+                ws_bytes = SG.warp_bytes;
+            }
+            residual_chunk_staged<(VPL <= 2 ? VPL : 2), BF16, HINT>(D, (int32_t)c, lane, ws, pol);
+        } else {
+            residual_chunk<L, VPL, BF16, HINT>(D, (int32_t)c, lane, pol);
+        }
+    }
+    // the last CTA out resets the tickets for the next launch (stream order makes it visible)
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         int done = atomicAdd(ctrl + 1, 1);
         if (done == (int)gridDim.x - 1) {
             atomicExch(ctrl + 0, 0);
+            atomicExch(ctrl + 3, 0);
             atomicExch(ctrl + 1, 0);
         }
     }
@@ -505,10 +753,12 @@ void fill_desc(const Plan* P, const void* B, int64_t ldb, float* C, int64_t ldc,
     d->n_rl = (int32_t)P->st.n_rl;
     d->n_res = (int32_t)P->st.n_res;
     d->rl_all = P->st.n_rl == P->st.m ? 1 : 0;
+    d->hot = P->hot_bits;
+    d->chunk_nnz = P->tune.chunk_nnz;
     d->status = P->ctrl + 2;
 }
 
-typedef void (*ExecKernel)(const ExecDesc*, const int32_t*, const int32_t*, int64_t, int32_t*);
+typedef void (*ExecKernel)(const ExecDesc*, const int32_t*, const int32_t*, int64_t, int32_t*, ExecDesc);
 
 template <bool BF16, bool HINT, bool DENSE>
 static ExecKernel pick_kernel(int K)
@@ -546,14 +796,31 @@ int num_sms(int device)
     return cached[device];
 }
 
+// dynamic shared memory of one execute CTA: the dense item's tiles (phase 1) or the residual
+// warps' staging rings (phase 2), whichever is larger
+static size_t exec_smem_bytes(int K, int TM, int TK, bool bf16, bool dense, int W)
+{
+    // (L, VPL) exactly as pick_kernel chooses the instantiation
+    const int nv = K / 4;
+    const int L = nv <= 2 ? 2 : (nv <= 4 ? 4 : (nv <= 8 ? 8 : (nv <= 16 ? 16 : 32)));
+    const int VPL = nv <= 32 ? 1 : (nv <= 64 ? 2 : (nv <= 128 ? 4 : 8));
+    size_t b = staged_path(L, VPL) ? (size_t)kExecWarps * stage_geom(K, bf16, W).warp_bytes : 0;
+    // (chunk_nnz <= 1024 keeps this within the 227 KB a CTA may use)
+    if (dense) {
+        size_t d = dense_smem_bytes(K, TM, TK, bf16);
+        if (d > b) b = d;
+    }
+    return b;
+}
+
 // Kernel attributes and the persistent grid (resident CTAs on every SM, at most n_items).
 // Must run outside stream capture.
 ns_status_t exec_prepare(int64_t n_items, int K, int TM, int TK, bool bf16, bool hint, bool dense,
-                         int* grid_out)
+                         int* grid_out, int W)
 {
     ExecKernel kern = select_kernel(K, bf16, hint, dense);
-    const size_t smem = dense ? dense_smem_bytes(K, TM, TK, bf16) : 0;
-    if (dense) NS_TRY(dense_prepare(reinterpret_cast<const void*>(kern), smem));
+    const size_t smem = exec_smem_bytes(K, TM, TK, bf16, dense, W);
+    if (smem > 48 * 1024) NS_TRY(dense_prepare(reinterpret_cast<const void*>(kern), smem));
     int per_sm = 0;
     NS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kExecThreads, smem));
     if (per_sm < 1) per_sm = 1;
@@ -571,24 +838,33 @@ ns_status_t exec_prepare(int64_t n_items, int K, int TM, int TK, bool bf16, bool
 // the occupancy-derived grid between launches (0 = compute).
 ns_status_t exec_launch(const ExecDesc* descs, const int32_t* queue, const int32_t* queue_desc,
                         int64_t n_items, int32_t* ctrl, int K, int TM, int TK, bool bf16, bool hint,
-                        bool dense, int* grid_cache, cudaStream_t s)
+                        bool dense, int* grid_cache, cudaStream_t s, const ExecDesc* d0, int W)
 {
     ExecKernel kern = select_kernel(K, bf16, hint, dense);
-    const size_t smem = dense ? dense_smem_bytes(K, TM, TK, bf16) : 0;
+    const size_t smem = exec_smem_bytes(K, TM, TK, bf16, dense, W);
     int grid = grid_cache ? *grid_cache : 0;
-    if (grid == 0) NS_TRY(exec_prepare(n_items, K, TM, TK, bf16, hint, dense, &grid));
+    if (grid == 0) NS_TRY(exec_prepare(n_items, K, TM, TK, bf16, hint, dense, &grid, W));
     if (grid_cache) *grid_cache = grid;
     if (n_items == 0) return NS_OK;
-    kern<<<grid, kExecThreads, smem, s>>>(descs, queue, queue_desc, n_items, ctrl);
+    ExecDesc dv{};
+    if (d0) dv = *d0;
+    kern<<<grid, kExecThreads, smem, s>>>(d0 ? nullptr : descs, queue, queue_desc, n_items, ctrl, dv);
     NS_LAUNCH_CHECK();
     return NS_OK;
 }
 
+// single plan: the descriptor travels as a kernel parameter (no upload per launch)
 ns_status_t exec_launch_plan(Plan* P, cudaStream_t s)
 {
-    return exec_launch(P->desc_dev, P->queue, nullptr, P->st.n_items, P->ctrl, P->K, P->tune.TM,
+    const int K = P->desc_host.K;  // the column slice of this launch
+    int* gc = K == P->K ? &P->exec_grid : &P->exec_grid_slice;
+    if (K != P->K && P->exec_grid_slice_K != K) {
+        P->exec_grid_slice = 0;
+        P->exec_grid_slice_K = K;
+    }
+    return exec_launch(nullptr, P->queue, nullptr, P->st.n_items, P->ctrl, K, P->tune.TM,
                        P->tune.TK, P->dtype == NS_BF16, P->tune.l2_hints != 0, P->st.n_dwin > 0,
-                       &P->exec_grid, s);
+                       gc, s, &P->desc_host, P->tune.chunk_nnz);
 }
 
 }  // namespace ns

@@ -56,8 +56,12 @@ enum : int32_t {
 };
 
 // ---------------------------------------------------------------------------------------------
-// stream-ordered device allocations (cudaMallocAsync pool)
+// stream-ordered device allocations from the library's own memory pool
 // ---------------------------------------------------------------------------------------------
+// The pool keeps freed blocks mapped (release threshold = max) so that planning again does not
+// re-map physical memory at every synchronisation; ns_release_cache trims it.
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
+void pool_trim();
 struct DevBlock {
     void* ptr = nullptr;
     size_t bytes = 0;
@@ -128,6 +132,8 @@ struct ExecDesc {
     int32_t m, n;          // shape of A (bounds guards)
     int32_t n_rl, n_res;   // residual list rows, residual nonzeros (bounds guards)
     int32_t rl_all;        // 1: the residual list is every row in order (contiguous stream)
+    const uint32_t* hot;   // bit j set: B row j is among the most gathered (evict-last); null: all
+    int32_t chunk_nnz;     // W of the plan (sizes the staged chunk buffers)
     int32_t* status;       // device status word (kStatus* bits)
 };
 
@@ -173,16 +179,19 @@ struct Plan {
     int32_t* split_base = nullptr;
     int32_t* queue = nullptr;
     int64_t* item_cost = nullptr;
+    uint32_t* hot_bits = nullptr;    // execution hint (l2_hints == 2): hot B rows, n bits
     // execution scratch
     float* slots = nullptr;
     int32_t* split_cnt = nullptr;
     int32_t* ctrl = nullptr;       // [0] ticket, [1] CTAs done, [2] status, [3..] scalars
-    ExecDesc* desc_dev = nullptr;  // one ExecDesc, refreshed when B/C change
-    ExecDesc desc_host{};
+    ExecDesc desc_host{};           // the single-plan descriptor (a kernel parameter)
     bool desc_valid = false;
     std::vector<DevBlock> blocks;  // every device allocation the plan owns
     int exec_grid = 0;
+    int exec_grid_slice = 0, exec_grid_slice_K = 0;  // grid of the column-slice launches
     cudaStream_t last_stream = nullptr;  // stream of the last plan/execute call: frees go there
+    int32_t* status_host = nullptr;      // pinned copy of the device status word after a launch
+    cudaEvent_t status_ev = nullptr;     // completes when that copy has landed
     ~Plan();
 };
 
@@ -210,10 +219,11 @@ ns_status_t plan_check_tune(const ns_tune_t& t);
 void fill_desc(const Plan* P, const void* B, int64_t ldb, float* C, int64_t ldc, ExecDesc* d);
 ns_status_t exec_launch(const ExecDesc* descs, const int32_t* queue, const int32_t* queue_desc,
                         int64_t n_items, int32_t* ctrl, int K, int TM, int TK, bool bf16, bool hint,
-                        bool dense, int* grid_cache, cudaStream_t s);
+                        bool dense, int* grid_cache, cudaStream_t s, const ExecDesc* d0 = nullptr,
+                        int W = 256);
 ns_status_t exec_launch_plan(Plan* P, cudaStream_t s);
 ns_status_t exec_prepare(int64_t n_items, int K, int TM, int TK, bool bf16, bool hint, bool dense,
-                         int* grid_out);
+                         int* grid_out, int W = 256);
 ns_status_t plan_create(const ns_csr_t* A, int32_t K, ns_dtype_t dt, const ns_tune_t* tune,
                         cudaStream_t s, Plan** out);  // checks + build; on error nothing is kept
 

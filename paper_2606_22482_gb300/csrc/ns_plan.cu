@@ -241,6 +241,61 @@ __global__ void k_bucket_offsets(int32_t* hist, int64_t nblocks)
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// hot B rows (Section 6.2.1: the rows of B gathered most often are kept in L2, capped at about
+// 80% of its capacity; the rest bypass).  Execution hint only, not part of the partition.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_gather_counts(const int32_t* __restrict__ col, int64_t nres, int32_t n, int32_t* cnt)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p - lane < nres;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = p < nres ? __ldg(col + p) : -1;
+        // one atomic per distinct column per warp (hub columns repeat inside a warp)
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        if (c >= 0 && c < n && (__ffs(peers) - 1) == lane) atomicAdd(cnt + c, __popc(peers));
+    }
+}
+
+// 64 bins of floor(log2(count)) over the columns
+__global__ void k_count_bins(const int32_t* __restrict__ cnt, int32_t n, unsigned long long* bins)
+{
+    __shared__ unsigned long long sb[64];
+    if (threadIdx.x < 64) sb[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cnt[j];
+        if (c > 0) atomicAdd(&sb[31 - __clz(c)], 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x < 64 && sb[threadIdx.x]) atomicAdd(bins + threadIdx.x, sb[threadIdx.x]);
+}
+
+// threshold: the smallest power of two h such that the columns with count >= h fit in `cap` rows
+__global__ void k_hot_threshold(const unsigned long long* bins, int64_t cap, int32_t* h_out)
+{
+    if (threadIdx.x != 0) return;
+    unsigned long long acc = 0;
+    int b = 31;
+    for (; b >= 0; --b) {
+        if (acc + bins[b] > (unsigned long long)cap) break;
+        acc += bins[b];
+    }
+    *h_out = b >= 31 ? 0x7fffffff : (1 << (b + 1));  // counts >= 2^(b+1) are hot
+}
+
+__global__ void k_hot_bits(const int32_t* __restrict__ cnt, int32_t n, const int32_t* h, uint32_t* bits)
+{
+    const int lane = threadIdx.x & 31;
+    const int32_t th = *h;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j - lane < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const bool hot = j < n && cnt[j] >= th;
+        const unsigned b = __ballot_sync(0xffffffffu, hot);
+        if (lane == 0 && j < n) bits[j >> 5] = b;
+    }
+}
+
 // fill with a 32-bit value
 __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v)
 {
@@ -259,10 +314,12 @@ ns_status_t plan_check_tune(const ns_tune_t& t)
 {
     if (!(t.TM == 16 || t.TM == 32 || t.TM == 64)) return NS_ERR_INVALID;
     if (!(t.TK == 16 || t.TK == 32)) return NS_ERR_INVALID;
-    if (t.chunk_nnz < 2 || t.chunk_nnz > (1 << 20)) return NS_ERR_INVALID;
+    if (t.chunk_nnz < 2 || t.chunk_nnz > 1024) return NS_ERR_INVALID;  // chunk buffers fit a CTA
     if (t.group != kExecWarps) return NS_ERR_INVALID;
     if (t.cost_tc < 0 || t.cost_res < 0 || t.absorb_cap < 0) return NS_ERR_INVALID;
     if (t.col_order != 0 && t.col_order != 1) return NS_ERR_INVALID;
+    if (t.TN < 0 || (t.TN % 8) != 0) return NS_ERR_INVALID;
+    if (t.l2_hints < 0 || t.l2_hints > 2) return NS_ERR_INVALID;
     return NS_OK;
 }
 
@@ -370,7 +427,6 @@ ns_status_t plan_build(Plan* P, const ns_csr_t* A, int32_t K, ns_dtype_t dt, con
         a.reserve(&P->ctrl, 8);
         a.reserve(&counters, 8);
         a.reserve(&totals, 16);
-        a.reserve(&P->desc_dev, 1);
         NS_TRY(a.commit(s));
         P->blocks.push_back(a.take());
         NS_CUDA_TRY(cudaMemsetAsync(P->ctrl, 0, sizeof(int32_t) * 8, s));
@@ -436,6 +492,39 @@ ns_status_t plan_build(Plan* P, const ns_csr_t* A, int32_t K, ns_dtype_t dt, con
         NS_LAUNCH_CHECK();
     }
     NS_TRY(splits_and_queue(P, windows_on ? &win : nullptr, s, totals));
+
+    // ---- hot B rows for the L2 policy (l2_hints == 2) ----
+    if (tune->l2_hints == 2 && n > 0) {
+        Arena h;
+        int32_t* cnt = nullptr;
+        unsigned long long* bins = nullptr;
+        int32_t* th = nullptr;
+        h.reserve(&cnt, n);
+        h.reserve(&bins, 64);
+        h.reserve(&th, 1);
+        NS_TRY(h.commit(s));
+        Arena hb;
+        hb.reserve(&P->hot_bits, ceil_div(n, 32));
+        NS_TRY(hb.commit(s));
+        P->blocks.push_back(hb.take());
+        NS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n, s));
+        NS_CUDA_TRY(cudaMemsetAsync(bins, 0, sizeof(unsigned long long) * 64, s));
+        if (P->st.n_res > 0) {
+            k_gather_counts<<<grid_for(P->st.n_res), 256, 0, s>>>(P->res_col, P->st.n_res, (int32_t)n, cnt);
+            NS_LAUNCH_CHECK();
+        }
+        k_count_bins<<<grid_for(n), 256, 0, s>>>(cnt, (int32_t)n, bins);
+        NS_LAUNCH_CHECK();
+        int l2 = 0;
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, P->device);
+        const int64_t row_bytes = (int64_t)K * (dt == NS_BF16 ? 2 : 4);
+        const int64_t cap = (int64_t)(0.8 * (double)(l2 > 0 ? l2 : (96 << 20))) / row_bytes;
+        k_hot_threshold<<<1, 32, 0, s>>>(bins, cap, th);
+        NS_LAUNCH_CHECK();
+        k_hot_bits<<<grid_for(n), 256, 0, s>>>(cnt, (int32_t)n, th, P->hot_bits);
+        NS_LAUNCH_CHECK();
+        h.release(s);
+    }
 
     // ---- one readback: validation counters and split totals ----
     unsigned long long hc[8];

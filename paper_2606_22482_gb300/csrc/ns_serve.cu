@@ -208,7 +208,7 @@ static void worker_loop(Server* S)
             const size_t bS = ((size_t)P->st.n_slots * q->r.K * 4 + 255) & ~size_t(255);
             const size_t bN = ((size_t)(P->st.n_split > 0 ? P->st.n_split : 1) * 4 + 255) & ~size_t(255);
             void* blk = nullptr;
-            if (cudaMallocAsync(&blk, bB + bC + bS + bN, S->s_copy) != cudaSuccess) {
+            if (pool_alloc(&blk, bB + bC + bS + bN, S->s_copy) != cudaSuccess) {
                 (void)cudaGetLastError();
                 std::lock_guard<std::mutex> lk(S->mu);
                 fail_req(S, q, NS_ERR_OOM);
@@ -282,7 +282,7 @@ static void worker_loop(Server* S)
                 S->flip ^= 1;
                 const size_t bD = (descs.size() * sizeof(ExecDesc) + 255) & ~size_t(255);
                 const size_t bQ = ((size_t)(ni > 0 ? ni : 1) * 4 + 255) & ~size_t(255);
-                if (cudaMallocAsync(&L.block, bD + 2 * bQ + 256, L.stream) != cudaSuccess) {
+                if (pool_alloc(&L.block, bD + 2 * bQ + 256, L.stream) != cudaSuccess) {
                     (void)cudaGetLastError();
                     std::lock_guard<std::mutex> lk(S->mu);
                     for (SReq* q : rs) fail_req(S, q, NS_ERR_OOM);
@@ -302,7 +302,7 @@ static void worker_loop(Server* S)
                 cudaMemsetAsync(ctrl, 0, 256, L.stream);
                 int grid = 0;
                 ns_status_t r = exec_launch(dd, dq, dqd, ni, ctrl, K, TM, TK, bf16, S->cfg.tune.l2_hints != 0,
-                                            dense, &grid, L.stream);
+                                            dense, &grid, L.stream, nullptr, S->cfg.tune.chunk_nnz);
                 const double t_start = serve_clock();
                 for (SReq* q : rs) {
                     const SGraph& g = S->graphs[q->r.graph_id];

@@ -20,6 +20,7 @@ def tune_from(ns, **kw):
 def oracle_tune(t):
     d = t.as_dict()
     d.pop("l2_hints")
+    d.pop("TN")
     return d
 
 

@@ -158,3 +158,14 @@ def test_kernels_really_launch():
     A, B = synth.config_small(1)
     run(A, B, check_plan=False)
     assert ns.launch_count() > before
+
+
+@pytest.mark.parametrize("K,TN", [(128, 64), (128, 32), (256, 64), (96, 32), (64, 16)])
+def test_column_slices_bit_identical(K, TN):
+    # slicing the columns of B and C does not change any output element's summation order
+    A = synth.rmat_csr(12, 50000, seed=K + TN)
+    B = synth.dense_b(A["n"], K, seed=4)
+    c_full, ref = run(A, B, tune=tune_from(ns, TN=0), check_plan=False)
+    c_sl, _ = run(A, B, tune=tune_from(ns, TN=TN), check_plan=False)
+    assert np.array_equal(c_full, c_sl)
+    assert oracle.rel_frobenius(c_sl, ref) <= 1e-6

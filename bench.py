@@ -186,6 +186,7 @@ def main():
     ap.add_argument("--l2", type=int, default=None, choices=[0, 1, 2],
                     help="override the L2 policy of the tune (2: planner-marked hot B rows)")
     ap.add_argument("--tn", type=int, default=None, help="override the column-slice width TN")
+    ap.add_argument("--chunk", type=int, default=None, help="override the residual chunk size W")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -272,6 +273,10 @@ def main():
     if args.tn is not None:
         tune.TN = args.tn
         tune_src += f", TN={args.tn}"
+    if args.chunk is not None:
+        tune.chunk_nnz = args.chunk
+        tune.absorb_cap = args.chunk
+        tune_src += f", chunk_nnz={args.chunk}"
 
     def step(ev=None):
         p = ns.spmm_plan(At, K, DT, tune)

@@ -28,6 +28,7 @@ struct Batch {
     struct Group {              // graphs sharing K (one persistent launch each)
         int K = 0;
         bool dense = false;
+        bool contig = false;  // every plan of the group has a contiguous residual stream
         std::vector<int> graphs;
         ExecDesc* descs_dev = nullptr;
         int32_t* queue = nullptr;
@@ -132,6 +133,7 @@ ns_status_t ns_batch_plan(const ns_csr_t* As, int32_t count, const int32_t* Ks, 
         for (int gi = 0; gi < (int)G.graphs.size(); ++gi) {
             Plan* P = Bt->plans[G.graphs[gi]];
             G.dense = G.dense || P->st.n_dwin > 0;
+            G.contig = (gi == 0 || G.contig) && plan_contig(P);
             int64_t n = P->st.n_items;
             std::vector<int64_t> cost(n);
             std::vector<int32_t> q(n);
@@ -222,7 +224,8 @@ ns_status_t ns_batch_execute(ns_batch_t b, const void* const* Bs, float* const* 
     if (!Bt->exec) {
         // capture every group's persistent launch once; later calls replay the graph
         for (auto& G : Bt->groups)  // occupancy queries and attributes outside the capture
-            NS_TRY(exec_prepare(G.n_items, G.K, G.TM, G.TK, Bt->dtype == NS_BF16, Bt->hint, G.dense, &G.grid, G.W));
+            NS_TRY(exec_prepare(G.n_items, G.K, G.TM, G.TK, Bt->dtype == NS_BF16, Bt->hint, G.dense, &G.grid, G.W,
+                                G.contig));
         // the caller's stream may be the legacy default stream, which cannot be captured: record
         // the launches on a private stream once; the graph then replays on the caller's stream
         if (!Bt->cap_stream) NS_CUDA_TRY(cudaStreamCreateWithFlags(&Bt->cap_stream, cudaStreamNonBlocking));
@@ -230,7 +233,8 @@ ns_status_t ns_batch_execute(ns_batch_t b, const void* const* Bs, float* const* 
         ns_status_t r = NS_OK;
         for (auto& G : Bt->groups) {
             r = exec_launch(G.descs_dev, G.queue, G.queue_desc, G.n_items, G.ctrl, G.K, G.TM, G.TK,
-                            Bt->dtype == NS_BF16, Bt->hint, G.dense, &G.grid, Bt->cap_stream, nullptr, G.W);
+                            Bt->dtype == NS_BF16, Bt->hint, G.dense, &G.grid, Bt->cap_stream, nullptr, G.W,
+                            G.contig);
             if (r != NS_OK) break;
         }
         cudaGraph_t graph = nullptr;
@@ -404,6 +408,33 @@ ns_status_t ns_autotune(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, ns_str
                 release();
                 return r;
             }
+        }
+    }
+    // residual chunk size W and the L2 policy of the best configuration so far
+    {
+        const ns_tune_t base_best = best;
+        const int32_t Ws[3] = {128, 512, 1024};
+        for (int32_t w : Ws) {
+            if (w == base_best.chunk_nnz) continue;
+            ns_tune_t t = base_best;
+            t.chunk_nnz = w;
+            t.absorb_cap = w;
+            double ex = 0, pl = 0;
+            r = time_tune(A, K, b_dtype, t, Bd, Cd, st, &ex, &pl, nullptr);
+            if (r == NS_OK) consider(t, ex, pl);
+            else if (r != NS_ERR_UNSUPPORTED) {
+                release();
+                return r;
+            }
+        }
+        ns_tune_t t = best;
+        t.l2_hints = 2;
+        double ex = 0, pl = 0;
+        r = time_tune(A, K, b_dtype, t, Bd, Cd, st, &ex, &pl, nullptr);
+        if (r == NS_OK) consider(t, ex, pl);
+        else if (r != NS_ERR_UNSUPPORTED) {
+            release();
+            return r;
         }
     }
     // column slices (Section 6.2.2 N shaping): narrower passes keep the gathered B rows in L2

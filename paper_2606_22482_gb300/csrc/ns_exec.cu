@@ -269,40 +269,29 @@ __device__ __noinline__ void deliver_split_row(const ExecDesc& D, int32_t row, i
     if (lane == 0) atomicExch(D.split_cnt + s, 0);
 }
 
-// Residual chunk when the residual list is every row in order (no dense windows) and
-// 128 <= K <= 256 (one nonzero per warp step, 32 lanes x 4 columns x VPL).  The chunk's nonzeros
-// are one contiguous stream.  Gathered B rows go through a kStages-deep ring in this warp's shared
-// memory with cp.async (Section 7's double-buffer pipelining, deepened): while stage s is summed,
-// stages s+1 .. s+kStages-1 are in flight, so the bytes in flight cost no registers.  Column ids
-// and values of the next stage are loaded one stage ahead, row ends and split ids 32 rows at a time.
-constexpr int kStages = 3;
+// ---------------------------------------------------------------------------------------------
+// residual chunks with K <= 256: decoded chunk in shared memory, gathers through a register ring
+// ---------------------------------------------------------------------------------------------
+// A chunk holds at most 3W/2 merge items (boundaries snap by less than W/2), so its rows and its
+// nonzero stream fit in `cap` entries.  Per warp, shared memory holds the decoded chunk: the
+// nonzeros as (column, value) pairs (padded by the ring depth), and per row its id, split id,
+// first and past-last stream positions and first residual index.
+constexpr int kRing = 8;  // gathered rows in flight per warp (K <= 128; 4 for K <= 256)
 
 struct StageGeom {
-    int NB;          // nonzeros per stage
-    int rowbytes;    // one gathered B row (a multiple of 16 bytes since K % 8 == 0)
-    int stage_bytes; // NB * rowbytes
-    int cap;         // capacity of the chunk's (col, val) stream in shared memory
-    int off_col, off_val, bars_off;
+    int cap;         // capacity of the chunk's stream and of its row arrays
+    int rows_off;    // byte offset of the row arrays (after cap + kRing (col, val) pairs)
     int warp_bytes;  // shared memory of one warp, a multiple of 128
 };
 
-// A chunk holds at most 3W/2 merge items (boundaries snap by less than W/2), so its rows and its
-// nonzero stream fit in `cap` entries.  Per warp, shared memory holds the decoded chunk:
-// column ids and values (padded by the ring depth), and per row its id, split id, and first and
-// past-last stream positions, plus the rows' first residual index (general residual lists).
-constexpr int kRing = 8;  // gathered rows in flight per warp (K <= 128; 4 for K <= 256)
-
 __host__ __device__ inline StageGeom stage_geom(int K, bool bf16, int W)
 {
+    (void)K;
+    (void)bf16;
     StageGeom g;
-    g.rowbytes = K * (bf16 ? 2 : 4);
-    g.NB = 0;
-    g.stage_bytes = 0;
     g.cap = ((3 * W) / 2 + 32 + 31) & ~31;
-    g.off_col = 0;                               // cap + kRing int32
-    g.off_val = 4 * (g.cap + kRing);             // cap + kRing float
-    g.bars_off = 8 * (g.cap + kRing);            // row arrays: 4 x (cap + 1) int32, cap int64
-    g.warp_bytes = (g.bars_off + 16 * (g.cap + 1) + 8 * g.cap + 127) & ~127;
+    g.rows_off = 8 * (g.cap + kRing);
+    g.warp_bytes = (g.rows_off + 16 * (g.cap + 1) + 8 * g.cap + 127) & ~127;
     return g;
 }
 
@@ -315,26 +304,6 @@ __device__ __forceinline__ uint32_t dynamic_smem_bytes()
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
     return r;
 }
-
-template <int VPL, bool BF16>
-__device__ __forceinline__ float4 lds_vec(const unsigned char* row, int v)
-{
-    if (!BF16) return *reinterpret_cast<const float4*>(row + 16 * v);
-    const uint2 u = *reinterpret_cast<const uint2*>(row + 8 * v);
-    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
-                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
-}
-
-constexpr uint32_t kWaitLimit = 1u << 22;  // bounded mbarrier waits (far beyond any copy latency)
-
-// per-warp staging state that persists across the chunks a warp processes
-struct WarpStage {
-    unsigned char* base;  // kStages stages of rows, the chunk's columns and values, barriers
-    int32_t* cols;
-    float* vals;
-    uint64_t* bars;
-    uint32_t g0;          // stages consumed so far (barrier phase bookkeeping)
-};
 
 // Row metadata of up to 32 consecutive residual-list rows of a chunk, one row per lane, with the
 // rows' positions in the chunk's stream of nonzeros (rows clipped to the chunk's merge range).
@@ -385,19 +354,6 @@ __device__ __forceinline__ void load_win(const ExecDesc& D, RowWin& w, int64_t k
     w.total = base + __shfl_sync(0xffffffffu, inc, 31);
 }
 
-// Residual chunk with K <= 256 (at most two 4-column vectors per lane, one nonzero per warp step).
-// The chunk's nonzeros, over all its residual-list rows, form one stream.  Gathered B rows go
-// through a kStages-deep ring in this warp's shared memory (Section 7's double-buffer pipelining,
-// deepened): each row is ONE bulk asynchronous copy issued by the lane that holds its column and
-// completing on the stage's mbarrier, so the bytes in flight cost neither registers nor per-lane
-// instructions.  Column ids and values of the next stage are resolved and loaded one stage ahead.
-// one 4-column vector of a gathered B row at byte address p (16 B of FP32 or 8 B of BF16)
-template <bool BF16, bool HINT>
-__device__ __forceinline__ float4 ld_vec_at(const unsigned char* p, uint64_t pol)
-{
-    return ld_b4<BF16, HINT>(p, 0, pol);
-}
-
 // The streamed inner loop.  FULL: every lane holds VPL whole vectors (K == 128 * VPL), so no
 // per-lane width test; HOT: the planner's hot-row map picks each gather's L2 policy.
 template <int VPL, bool BF16, bool HINT, bool FULL, bool HOT>
@@ -412,7 +368,6 @@ __device__ __forceinline__ void stream_rows(const ExecDesc& D, int32_t c, int la
     const uint32_t ldb_bytes = (uint32_t)(D.ldb * (BF16 ? 2 : 4));
     float* const Cp = D.C;
     const int64_t ldc = D.ldc;
-    const uint32_t* const hotp = D.hot;
 
     float4 acc[VPL];
 #pragma unroll
@@ -446,13 +401,15 @@ __device__ __forceinline__ void stream_rows(const ExecDesc& D, int32_t c, int la
     float4 b[U][VPL];
     float w[U];
     auto gather = [&](int2 e, float4 (&dst)[VPL], float& wv) {
-        // padding entries point at a real row with value 0: no test needed here
-        const unsigned char* row = Bl + (size_t)(uint32_t)e.x * ldb_bytes;
+        // padding entries point at a real row with value 0: no test needed here.  With the hot
+        // map, bit 31 of the column id marks a hot row (set when the chunk was decoded).
+        const uint32_t col = HOT ? ((uint32_t)e.x & 0x7fffffffu) : (uint32_t)e.x;
+        const unsigned char* row = Bl + (size_t)col * ldb_bytes;
         uint64_t pl = pol.last;
-        if (HOT) pl = ((__ldg(hotp + (e.x >> 5)) >> (e.x & 31)) & 1u) ? pol.last : pol.first;
+        if (HOT) pl = e.x < 0 ? pol.last : pol.first;
 #pragma unroll
         for (int q = 0; q < VPL; ++q) {
-            if (FULL || lane + 32 * q < nv) dst[q] = ld_vec_at<BF16, HINT>(row + 32 * VB * q, pl);
+            if (FULL || lane + 32 * q < nv) dst[q] = ld_b4<BF16, HINT>(row + 32 * VB * q, 0, pl);
             else dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         wv = __int_as_float(e.y);
@@ -474,7 +431,7 @@ __device__ __forceinline__ void stream_rows(const ExecDesc& D, int32_t c, int la
 }
 
 template <int VPL, bool BF16, bool HINT>
-__device__ void residual_chunk_staged(const ExecDesc& D, int32_t c, int lane, WarpStage& ws,
+__device__ void residual_chunk_staged(const ExecDesc& D, int32_t c, int lane, unsigned char* wbase,
                                       const Policies& pol)
 {
     const StageGeom G = stage_geom(D.K, BF16, D.chunk_nnz);
@@ -488,8 +445,8 @@ __device__ void residual_chunk_staged(const ExecDesc& D, int32_t c, int lane, Wa
         if (lane == 0) atomicOr(D.status, kStatusInternal);
         return;
     }
-    int2* const ent = reinterpret_cast<int2*>(ws.base);  // (col, value bits), cap + kRing
-    int32_t* const rrow = reinterpret_cast<int32_t*>(ws.base + G.bars_off);
+    int2* const ent = reinterpret_cast<int2*>(wbase);  // (col, value bits), cap + kRing
+    int32_t* const rrow = reinterpret_cast<int32_t*>(wbase + G.rows_off);
     int32_t* const rsplit = rrow + (G.cap + 1);
     int32_t* const rbeg = rsplit + (G.cap + 1);
     int32_t* const rend = rbeg + (G.cap + 1);
@@ -554,16 +511,23 @@ __device__ void residual_chunk_staged(const ExecDesc& D, int32_t c, int lane, Wa
                 }
             }
         }
+        uint32_t hw[4];  // hot-map words of the columns (independent loads as well)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int P = P0 + 32 * u + lane;
+            if ((unsigned)cc[u] >= (unsigned)D.n) {  // guard: never gather outside B
+                if (P < total) atomicOr(D.status, kStatusInternal);
+                cc[u] = 0;
+                vv[u] = 0.f;
+            }
+            hw[u] = (D.hot && P < total) ? __ldg(D.hot + (cc[u] >> 5)) : 0u;
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int P = P0 + 32 * u + lane;
             if (P < total) {
-                if ((unsigned)cc[u] >= (unsigned)D.n) {  // guard: never gather outside B
-                    atomicOr(D.status, kStatusInternal);
-                    cc[u] = 0;
-                    vv[u] = 0.f;
-                }
-                ent[P] = make_int2(cc[u], __float_as_int(vv[u]));
+                const int32_t hotbit = (D.hot && ((hw[u] >> (cc[u] & 31)) & 1u)) ? (int32_t)0x80000000 : 0;
+                ent[P] = make_int2(cc[u] | hotbit, __float_as_int(vv[u]));
             }
         }
     }
@@ -628,8 +592,8 @@ namespace ns {
 // ---------------------------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------------------------
-// residual-only kernels are held to 64 registers (8 CTAs = 32 warps per SM: latency hiding for
-// the gathers); kernels with the tensor-core item keep their registers for the accumulators
+// residual-only kernels are held to 128 registers (4 CTAs = 16 warps per SM, each with an 8-deep
+// gather ring); kernels with the tensor-core item keep their registers for the accumulators
 template <int L, int VPL, bool BF16, bool HINT, bool DENSE>
 __global__ void __launch_bounds__(kExecThreads, DENSE ? 1 : 4) k_exec(const ExecDesc* __restrict__ descs,
                                                        const int32_t* __restrict__ queue,
@@ -661,8 +625,6 @@ __global__ void __launch_bounds__(kExecThreads, DENSE ? 1 : 4) k_exec(const Exec
         }
     }
     // phase 2: residual chunks, one warp each, in work-list order (no CTA barrier)
-    WarpStage ws{nullptr, nullptr, nullptr, nullptr, 0};
-    int ws_bytes = -1;
     for (;;) {
         int64_t u = 0;
         if (lane == 0) u = atomicAdd(ctrl + 3, 1);
@@ -674,24 +636,17 @@ __global__ void __launch_bounds__(kExecThreads, DENSE ? 1 : 4) k_exec(const Exec
         if (it < D.n_dwin) continue;
         const int64_t c = (int64_t)(it - D.n_dwin) * kExecWarps + (u % kExecWarps);
         if (c >= D.n_chunks) continue;
-        // K <= 256: the streamed path, which needs the shared memory the host sized for it
+        // K <= 256: the streamed path, which needs the shared memory the host sized for it; this
+        // warp's slice follows the descriptor's chunk geometry (plans of one batched launch may
+        // differ in W; nothing in it outlives a chunk)
         if constexpr (VPL <= 2) {
-            if (dynamic_smem_bytes() < (uint32_t)(kExecWarps * stage_geom(D.K, BF16, D.chunk_nnz).warp_bytes)) {
+            const StageGeom SG = stage_geom(D.K, BF16, D.chunk_nnz);
+            if (dynamic_smem_bytes() < (uint32_t)(kExecWarps * SG.warp_bytes)) {
                 if (lane == 0) atomicOr(D.status, kStatusInternal);  // guard: misconfigured launch
                 continue;
             }
-            const StageGeom SG = stage_geom(D.K, BF16, D.chunk_nnz);
-            if (SG.warp_bytes != ws_bytes) {  // (re)arm this warp's barriers for this geometry
-                __syncwarp();
-                ws.base = smem_raw + warp * SG.warp_bytes;
-                ws.cols = reinterpret_cast<int32_t*>(ws.base + SG.off_col);
-                ws.vals = reinterpret_cast<float*>(ws.base + SG.off_val);
-                ws.bars = nullptr;
-                __syncwarp();
-                ws.g0 = 0;
-                ws_bytes = SG.warp_bytes;
-            }
-            residual_chunk_staged<(VPL <= 2 ? VPL : 2), BF16, HINT>(D, (int32_t)c, lane, ws, pol);
+            residual_chunk_staged<(VPL <= 2 ? VPL : 2), BF16, HINT>(D, (int32_t)c, lane,
+                                                                    smem_raw + warp * SG.warp_bytes, pol);
         } else {
             residual_chunk<L, VPL, BF16, HINT>(D, (int32_t)c, lane, pol);
         }
@@ -710,8 +665,219 @@ __global__ void __launch_bounds__(kExecThreads, DENSE ? 1 : 4) k_exec(const Exec
 }
 
 // ---------------------------------------------------------------------------------------------
+// residual-only plans whose list is every row in order (tau_tile = inf): a chunk's nonzeros are
+// one contiguous range of A and its rows are k0 .. kL themselves.  No shared memory: the lanes
+// read column ids and values 32 at a time (two batches ahead) and broadcast them by shuffles,
+// read row ends and split ids 32 rows at a time, and gather B rows through a 4-deep register
+// ring.  At 64 registers 8 CTAs (32 warps) fit on an SM; the gathers of many independent warps
+// hide the latency spread of a power-law column stream better than deeper rings in fewer warps.
+// ---------------------------------------------------------------------------------------------
+constexpr int kCRing = 4;
+
+template <int VPL, bool BF16, bool HINT>
+__device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int lane, const Policies& pol,
+                                             float4* stash)
+{
+    const int4 h0 = __ldg(reinterpret_cast<const int4*>(D.chunk_rec + c));
+    const int4 h1 = __ldg(reinterpret_cast<const int4*>(D.chunk_rec + c) + 1);
+    const int32_t b0 = h0.x, k0 = h0.z, kL = h0.w, z0 = h1.x, total = h1.y;
+    const int nr = kL - k0 + 1;
+    if (k0 < 0 || kL >= D.n_rl || kL < k0 || h0.y <= b0 || total < 0 || z0 < 0 ||
+        (int64_t)z0 + total > D.n_res) {
+        if (lane == 0) atomicOr(D.status, kStatusInternal);  // guard: corrupt plan
+        return;
+    }
+    const int32_t* const colp = D.res_col + z0;
+    const float* const valp = D.res_val + z0;
+    const int nv = D.K >> 2;
+    constexpr int VB = BF16 ? 8 : 16;  // bytes of one 4-column vector
+    const unsigned char* const Bl = reinterpret_cast<const unsigned char*>(D.B) + VB * lane;
+    const uint32_t ldb_bytes = (uint32_t)(D.ldb * (BF16 ? 2 : 4));
+
+    // the last column id pads the ring past the chunk's end (value 0: a cached reload)
+    const int32_t clast = total > 0 ? ld_stream_i32<HINT>(colp + total - 1, pol.first) : 0;
+    auto batch = [&](int P0, int32_t& cc, float& vv) {
+        const int P = P0 + lane;
+        cc = clast;
+        vv = 0.f;
+        if (P < total) {
+            cc = ld_stream_i32<HINT>(colp + P, pol.first);
+            vv = ld_stream_f32<HINT>(valp + P, pol.first);
+        }
+        if ((unsigned)cc >= (unsigned)D.n) {  // guard: never gather outside B
+            atomicOr(D.status, kStatusInternal);
+            cc = 0;
+            vv = 0.f;
+        }
+    };
+    // lane j: stream end of row k0 + base + j (merge position of its end item, less b0 and the
+    // end items of the rows before it) and its split id
+    int32_t wend = 0x7fffffff, wsplit = -1;
+    auto rows = [&](int base) {
+        const int32_t k = k0 + base + lane;
+        wend = 0x7fffffff;
+        wsplit = -1;
+        if (k <= kL) {
+            wend = __ldg(D.rl_start + k + 1) - 1 - b0 - (k - k0);
+            wsplit = __ldg(D.row_split + k);
+        }
+    };
+
+    int32_t ca, cb, cn;
+    float va, vb, vn;
+    batch(0, ca, va);
+    batch(32, cb, vb);
+    rows(0);
+    float4 acc[VPL];
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 b[kCRing][VPL];
+    float w[kCRing];
+    auto gather = [&](int32_t col, float val, float4 (&dst)[VPL], float& wv) {
+        const unsigned char* row = Bl + (size_t)(uint32_t)col * ldb_bytes;
+#pragma unroll
+        for (int q = 0; q < VPL; ++q) {
+            if (lane + 32 * q < nv) dst[q] = ld_b4<BF16, HINT>(row + 32 * VB * q, 0, pol.last);
+            else dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        wv = val;
+    };
+#pragma unroll
+    for (int u = 0; u < kCRing; ++u)
+        gather(__shfl_sync(0xffffffffu, ca, u), __shfl_sync(0xffffffffu, va, u), b[u], w[u]);
+
+    // Row ends inside the stream.  Only the chunk's first and last rows can be split (a middle
+    // row lies inside the chunk's merge range, so no other chunk touches it); the last one ends
+    // after the loop.  A split first row parks its partial sum in shared memory and is delivered
+    // after the loop, so the loop has no call in it and the ring keeps its registers.
+    int r = 0;
+    bool parked = false;
+    int next_end = __shfl_sync(0xffffffffu, wend, 0);
+    auto advance = [&]() {
+#pragma unroll
+        for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ++r;
+        if ((r & 31) == 0) rows(r);
+        next_end = __shfl_sync(0xffffffffu, wend, r & 31);
+    };
+    auto flush = [&]() {  // inside the loop
+        const int32_t sp = __shfl_sync(0xffffffffu, wsplit, r & 31);
+        if (sp < 0) {
+            float* crow = D.C + (int64_t)(k0 + r) * D.ldc;
+#pragma unroll
+            for (int q = 0; q < VPL; ++q) {
+                const int v = lane + 32 * q;
+                if (v < nv) st_c4<HINT>(crow + 4 * v, acc[q], pol.first);
+            }
+        } else if (r == 0) {
+#pragma unroll
+            for (int q = 0; q < VPL; ++q) stash[32 * q + lane] = acc[q];
+            parked = true;
+        } else if (lane == 0) {
+            atomicOr(D.status, kStatusInternal);  // guard: a middle row marked split
+        }
+        advance();
+    };
+    auto flush_last = [&]() {  // after the loop (any row, split or not)
+        const int32_t sp = __shfl_sync(0xffffffffu, wsplit, r & 31);
+        if (sp < 0) {
+            float* crow = D.C + (int64_t)(k0 + r) * D.ldc;
+#pragma unroll
+            for (int q = 0; q < VPL; ++q) {
+                const int v = lane + 32 * q;
+                if (v < nv) st_c4<HINT>(crow + 4 * v, acc[q], pol.first);
+            }
+        } else {
+            deliver_split_row<VPL, HINT>(D, k0 + r, sp, c, acc[0], acc[VPL > 1 ? VPL - 1 : 0], lane, pol.first);
+        }
+        advance();
+    };
+
+    for (int P0 = 0; P0 < total; P0 += 32) {
+        batch(P0 + 64, cn, vn);  // two batches ahead
+        for (int j0 = 0; j0 < 32; j0 += kCRing) {
+            if (P0 + j0 >= total) break;
+#pragma unroll
+            for (int u = 0; u < kCRing; ++u) {
+                const int P = P0 + j0 + u;
+                if (P >= total) break;  // past the last nonzero: later row ends belong after the loop
+                while (P >= next_end) flush();
+#pragma unroll
+                for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], b[u][q], acc[q]);
+                // entry P + kCRing: in this batch or the next (warp-uniform choice)
+                const int sl = j0 + u + kCRing;
+                const bool nx = sl >= 32;
+                const int32_t col = __shfl_sync(0xffffffffu, nx ? cb : ca, sl & 31);
+                const float val = __shfl_sync(0xffffffffu, nx ? vb : va, sl & 31);
+                gather(col, val, b[u], w[u]);
+            }
+        }
+        ca = cb;
+        va = vb;
+        cb = cn;
+        vb = vn;
+    }
+    if (parked) {
+        float4 p[VPL];
+#pragma unroll
+        for (int q = 0; q < VPL; ++q) p[q] = stash[32 * q + lane];
+        deliver_split_row<VPL, HINT>(D, k0, __ldg(D.row_split + k0), c, p[0], p[VPL > 1 ? VPL - 1 : 0], lane,
+                                     pol.first);
+    }
+    while (r < nr) flush_last();  // rows ending at or after the last nonzero (and the last row)
+}
+
+template <int VPL, bool BF16, bool HINT>
+__global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : 5) k_exec_contig(
+    const ExecDesc* __restrict__ descs, const int32_t* __restrict__ queue,
+    const int32_t* __restrict__ queue_desc, int64_t n_items, int32_t* ctrl,
+    const __grid_constant__ ExecDesc d0)
+{
+    __shared__ float4 s_park[kExecWarps * 32 * VPL];  // one parked partial row per warp
+    const int lane = threadIdx.x & 31;
+    float4* const park = s_park + (threadIdx.x >> 5) * 32 * VPL;
+    Policies pol{0, 0};
+    if (HINT) pol = make_policies();
+    for (;;) {
+        int64_t u = 0;
+        if (lane == 0) u = atomicAdd(ctrl + 3, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        const int64_t t = u / kExecWarps;
+        if (t >= n_items) break;
+        const int32_t it = __ldg(queue + t);
+        const ExecDesc& D = descs ? descs[queue_desc ? __ldg(queue_desc + t) : 0] : d0;
+        if (it < D.n_dwin) continue;
+        const int64_t c = (int64_t)(it - D.n_dwin) * kExecWarps + (u % kExecWarps);
+        if (c >= D.n_chunks) continue;
+        if (!D.rl_all) {  // guard: launched for a plan without a contiguous residual stream
+            if (lane == 0) atomicOr(D.status, kStatusInternal);
+            continue;
+        }
+        contig_chunk<VPL, BF16, HINT>(D, (int32_t)c, lane, pol, park);
+    }
+    // the last CTA out resets the tickets for the next launch (stream order makes it visible)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        int done = atomicAdd(ctrl + 1, 1);
+        if (done == (int)gridDim.x - 1) {
+            atomicExch(ctrl + 0, 0);
+            atomicExch(ctrl + 3, 0);
+            atomicExch(ctrl + 1, 0);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------------
+// the residual list is every row in order and A itself is the residual (no window pass ran):
+// a chunk's nonzeros are one contiguous range of A and its rows are k0 .. kL
+bool plan_contig(const Plan* P)
+{
+    return P->tune.tau_tile == kTauInf && P->st.n_dwin == 0 && P->st.n_rl == P->st.m;
+}
+
 void fill_desc(const Plan* P, const void* B, int64_t ldb, float* C, int64_t ldc, ExecDesc* d)
 {
     *d = ExecDesc{};
@@ -722,6 +888,7 @@ void fill_desc(const Plan* P, const void* B, int64_t ldb, float* C, int64_t ldc,
     d->rl_start = P->rl_start;
     d->chunk_b = P->chunk_b;
     d->chunk_k0 = P->chunk_k0;
+    d->chunk_rec = P->chunk_rec;
     d->n_chunks = (int32_t)P->st.n_chunks;
     d->n_dwin = (int32_t)P->st.n_dwin;
     d->win_rows = P->win_rows;
@@ -752,7 +919,7 @@ void fill_desc(const Plan* P, const void* B, int64_t ldb, float* C, int64_t ldc,
     d->n = (int32_t)P->st.n;
     d->n_rl = (int32_t)P->st.n_rl;
     d->n_res = (int32_t)P->st.n_res;
-    d->rl_all = P->st.n_rl == P->st.m ? 1 : 0;
+    d->rl_all = plan_contig(P) ? 1 : 0;
     d->hot = P->hot_bits;
     d->chunk_nnz = P->tune.chunk_nnz;
     d->status = P->ctrl + 2;
@@ -774,8 +941,19 @@ static ExecKernel pick_kernel(int K)
     return k_exec<32, 8, BF16, HINT, DENSE>;
 }
 
-static ExecKernel select_kernel(int K, bool bf16, bool hint, bool dense)
+template <bool BF16, bool HINT>
+static ExecKernel pick_contig(int K)
 {
+    return K <= 128 ? k_exec_contig<1, BF16, HINT> : k_exec_contig<2, BF16, HINT>;
+}
+
+// contig: a residual-only launch whose plans all have a contiguous residual stream (K <= 256)
+static ExecKernel select_kernel(int K, bool bf16, bool hint, bool dense, bool contig)
+{
+    if (contig && !dense && K <= 256) {
+        if (bf16) return hint ? pick_contig<true, true>(K) : pick_contig<true, false>(K);
+        return hint ? pick_contig<false, true>(K) : pick_contig<false, false>(K);
+    }
     if (bf16) {
         if (hint) return dense ? pick_kernel<true, true, true>(K) : pick_kernel<true, true, false>(K);
         return dense ? pick_kernel<true, false, true>(K) : pick_kernel<true, false, false>(K);
@@ -798,8 +976,9 @@ int num_sms(int device)
 
 // dynamic shared memory of one execute CTA: the dense item's tiles (phase 1) or the residual
 // warps' staging rings (phase 2), whichever is larger
-static size_t exec_smem_bytes(int K, int TM, int TK, bool bf16, bool dense, int W)
+static size_t exec_smem_bytes(int K, int TM, int TK, bool bf16, bool dense, int W, bool contig)
 {
+    if (contig && !dense && K <= 256) return 0;  // the contiguous-stream kernel keeps no staging
     // (L, VPL) exactly as pick_kernel chooses the instantiation
     const int nv = K / 4;
     const int L = nv <= 2 ? 2 : (nv <= 4 ? 4 : (nv <= 8 ? 8 : (nv <= 16 ? 16 : 32)));
@@ -816,10 +995,10 @@ static size_t exec_smem_bytes(int K, int TM, int TK, bool bf16, bool dense, int 
 // Kernel attributes and the persistent grid (resident CTAs on every SM, at most n_items).
 // Must run outside stream capture.
 ns_status_t exec_prepare(int64_t n_items, int K, int TM, int TK, bool bf16, bool hint, bool dense,
-                         int* grid_out, int W)
+                         int* grid_out, int W, bool contig)
 {
-    ExecKernel kern = select_kernel(K, bf16, hint, dense);
-    const size_t smem = exec_smem_bytes(K, TM, TK, bf16, dense, W);
+    ExecKernel kern = select_kernel(K, bf16, hint, dense, contig);
+    const size_t smem = exec_smem_bytes(K, TM, TK, bf16, dense, W, contig);
     if (smem > 48 * 1024) NS_TRY(dense_prepare(reinterpret_cast<const void*>(kern), smem));
     int per_sm = 0;
     NS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kExecThreads, smem));
@@ -838,12 +1017,13 @@ ns_status_t exec_prepare(int64_t n_items, int K, int TM, int TK, bool bf16, bool
 // the occupancy-derived grid between launches (0 = compute).
 ns_status_t exec_launch(const ExecDesc* descs, const int32_t* queue, const int32_t* queue_desc,
                         int64_t n_items, int32_t* ctrl, int K, int TM, int TK, bool bf16, bool hint,
-                        bool dense, int* grid_cache, cudaStream_t s, const ExecDesc* d0, int W)
+                        bool dense, int* grid_cache, cudaStream_t s, const ExecDesc* d0, int W,
+                        bool contig)
 {
-    ExecKernel kern = select_kernel(K, bf16, hint, dense);
-    const size_t smem = exec_smem_bytes(K, TM, TK, bf16, dense, W);
+    ExecKernel kern = select_kernel(K, bf16, hint, dense, contig);
+    const size_t smem = exec_smem_bytes(K, TM, TK, bf16, dense, W, contig);
     int grid = grid_cache ? *grid_cache : 0;
-    if (grid == 0) NS_TRY(exec_prepare(n_items, K, TM, TK, bf16, hint, dense, &grid, W));
+    if (grid == 0) NS_TRY(exec_prepare(n_items, K, TM, TK, bf16, hint, dense, &grid, W, contig));
     if (grid_cache) *grid_cache = grid;
     if (n_items == 0) return NS_OK;
     ExecDesc dv{};
@@ -864,7 +1044,7 @@ ns_status_t exec_launch_plan(Plan* P, cudaStream_t s)
     }
     return exec_launch(nullptr, P->queue, nullptr, P->st.n_items, P->ctrl, K, P->tune.TM,
                        P->tune.TK, P->dtype == NS_BF16, P->tune.l2_hints != 0, P->st.n_dwin > 0,
-                       gc, s, &P->desc_host, P->tune.chunk_nnz);
+                       gc, s, &P->desc_host, P->tune.chunk_nnz, plan_contig(P));
 }
 
 }  // namespace ns

@@ -97,6 +97,14 @@ struct Arena {
 // ---------------------------------------------------------------------------------------------
 // the device-side description of one plan's execution (read by the persistent kernel)
 // ---------------------------------------------------------------------------------------------
+// Execution-side summary of one merge-path chunk (derived from the plan's chunk boundaries, not
+// part of the canonical plan): merge range [b0, b1), residual-list rows k0 .. kL with an item in
+// the range, the residual index of the chunk's first nonzero (the whole chunk's nonzeros are
+// z0 .. z0 + total - 1 when the residual list is every row in order) and its nonzero count.
+struct alignas(32) ChunkRec {
+    int32_t b0, b1, k0, kL, z0, total, pad0, pad1;
+};
+
 struct ExecDesc {
     // residual CSR and its chunks
     const int32_t* res_rowptr;
@@ -106,6 +114,7 @@ struct ExecDesc {
     const int32_t* rl_start;
     const int32_t* chunk_b;
     const int32_t* chunk_k0;
+    const ChunkRec* chunk_rec;
     int32_t n_chunks;
     int32_t n_dwin;
     // dense windows and tiles
@@ -172,6 +181,7 @@ struct Plan {
     int32_t* rl_start = nullptr;
     int32_t* chunk_b = nullptr;
     int32_t* chunk_k0 = nullptr;
+    ChunkRec* chunk_rec = nullptr;  // per chunk, for the execute kernel
     int32_t* row_split = nullptr;
     int32_t* split_row = nullptr;
     int32_t* split_np = nullptr;
@@ -220,10 +230,11 @@ void fill_desc(const Plan* P, const void* B, int64_t ldb, float* C, int64_t ldc,
 ns_status_t exec_launch(const ExecDesc* descs, const int32_t* queue, const int32_t* queue_desc,
                         int64_t n_items, int32_t* ctrl, int K, int TM, int TK, bool bf16, bool hint,
                         bool dense, int* grid_cache, cudaStream_t s, const ExecDesc* d0 = nullptr,
-                        int W = 256);
+                        int W = 256, bool contig = false);
 ns_status_t exec_launch_plan(Plan* P, cudaStream_t s);
 ns_status_t exec_prepare(int64_t n_items, int K, int TM, int TK, bool bf16, bool hint, bool dense,
-                         int* grid_out, int W = 256);
+                         int* grid_out, int W = 256, bool contig = false);
+bool plan_contig(const Plan* P);  // contiguous residual stream (tau_tile = inf)
 ns_status_t plan_create(const ns_csr_t* A, int32_t K, ns_dtype_t dt, const ns_tune_t* tune,
                         cudaStream_t s, Plan** out);  // checks + build; on error nothing is kept
 

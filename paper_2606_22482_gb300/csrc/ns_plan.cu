@@ -99,22 +99,49 @@ __global__ void k_rl_all_rows(const int32_t* __restrict__ rowptr, int32_t m, int
 // item falls in a residual row with 2*(len+1) <= W, in which case it moves to the row's start.
 // rl_start must be non-decreasing (guaranteed for valid inputs; clamped otherwise).
 // ---------------------------------------------------------------------------------------------
-__global__ void k_chunks(const int32_t* __restrict__ rl_start, int64_t n_rl, int64_t T, int64_t W,
-                         int64_t nc, int32_t* chunk_b, int32_t* chunk_k0)
+__device__ __forceinline__ int64_t chunk_boundary(const int32_t* __restrict__ rl_start, int64_t n_rl,
+                                                  int64_t T, int64_t W, int64_t nc, int64_t c)
+{
+    if (c == 0) return 0;
+    if (c >= nc) return T;
+    const int64_t d = c * W;
+    const int64_t k = upper_minus_one(rl_start, n_rl, d);
+    const int64_t rlen = (int64_t)__ldg(rl_start + k + 1) - __ldg(rl_start + k) - 1;
+    return (2 * (rlen + 1) <= W) ? (int64_t)__ldg(rl_start + k) : d;
+}
+
+// also the execution-side chunk records: rows k0 .. kL with an item in [b0, b1) (row kL + 1
+// starts at or after b1), and the nonzero count = items - row ends inside the range (rows
+// k0 .. kL - 1 end inside it, row kL when its end item precedes b1)
+__global__ void k_chunks(const int32_t* __restrict__ rl_start, const int32_t* __restrict__ rl_rows,
+                         const int32_t* __restrict__ res_rowptr, int64_t m, int64_t n_rl, int64_t T,
+                         int64_t W, int64_t nc, int32_t* chunk_b, int32_t* chunk_k0, ChunkRec* rec)
 {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= nc;
          c += (int64_t)gridDim.x * blockDim.x) {
-        int64_t b;
-        if (c == 0) b = 0;
-        else if (c == nc) b = T;
-        else {
-            int64_t d = c * W;
-            int64_t k = upper_minus_one(rl_start, n_rl, d);
-            int64_t rlen = (int64_t)__ldg(rl_start + k + 1) - __ldg(rl_start + k) - 1;
-            b = (2 * (rlen + 1) <= W) ? (int64_t)__ldg(rl_start + k) : d;
-        }
+        const int64_t b = chunk_boundary(rl_start, n_rl, T, W, nc, c);
         chunk_b[c] = (int32_t)b;
-        if (c < nc) chunk_k0[c] = (int32_t)upper_minus_one(rl_start, n_rl, b);
+        if (c < nc) {
+            const int64_t k0 = upper_minus_one(rl_start, n_rl, b);
+            chunk_k0[c] = (int32_t)k0;
+            const int64_t b1 = chunk_boundary(rl_start, n_rl, T, W, nc, c + 1);
+            int64_t kL = (c + 1 < nc) ? upper_minus_one(rl_start, n_rl, b1) : n_rl - 1;
+            if (kL > k0 && (int64_t)__ldg(rl_start + kL) >= b1) --kL;
+            ChunkRec r;
+            r.b0 = (int32_t)b;
+            r.b1 = (int32_t)b1;
+            r.k0 = (int32_t)k0;
+            r.kL = (int32_t)kL;
+            r.total = -1;
+            r.z0 = -1;
+            if (k0 >= 0 && kL >= k0 && kL < n_rl) {
+                r.total = (int32_t)((b1 - b) - (kL - k0) - ((int64_t)__ldg(rl_start + kL + 1) <= b1 ? 1 : 0));
+                const int64_t i0 = __ldg(rl_rows + k0);
+                if (i0 >= 0 && i0 < m) r.z0 = (int32_t)((int64_t)__ldg(res_rowptr + i0) + (b - __ldg(rl_start + k0)));
+            }
+            r.pad0 = r.pad1 = 0;
+            rec[c] = r;
+        }
     }
 }
 
@@ -335,7 +362,8 @@ static ns_status_t splits_and_queue(Plan* P, const WindowResult* W, cudaStream_t
     const int64_t Wn = P->tune.chunk_nnz;
 
     if (nc > 0) {
-        k_chunks<<<grid_for(nc + 1), 256, 0, s>>>(P->rl_start, n_rl, T, Wn, nc, P->chunk_b, P->chunk_k0);
+        k_chunks<<<grid_for(nc + 1), 256, 0, s>>>(P->rl_start, P->rl_rows, P->res_rowptr, m, n_rl, T, Wn, nc,
+                                                   P->chunk_b, P->chunk_k0, P->chunk_rec);
         NS_LAUNCH_CHECK();
     } else {
         NS_CUDA_TRY(cudaMemsetAsync(P->chunk_b, 0, sizeof(int32_t), s));
@@ -477,6 +505,7 @@ ns_status_t plan_build(Plan* P, const ns_csr_t* A, int32_t K, ns_dtype_t dt, con
         }
         a.reserve(&P->chunk_b, nc + 1);
         a.reserve(&P->chunk_k0, nc);
+        a.reserve(&P->chunk_rec, nc);
         a.reserve(&P->row_split, m);
         a.reserve(&P->split_row, n_rl);  // split rows are residual-list rows
         a.reserve(&P->split_np, n_rl);

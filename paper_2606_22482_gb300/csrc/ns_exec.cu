@@ -666,17 +666,19 @@ __global__ void __launch_bounds__(kExecThreads, DENSE ? 1 : 4) k_exec(const Exec
 
 // ---------------------------------------------------------------------------------------------
 // residual-only plans whose list is every row in order (tau_tile = inf): a chunk's nonzeros are
-// one contiguous range of A and its rows are k0 .. kL themselves.  No shared memory: the lanes
-// read column ids and values 32 at a time (two batches ahead) and broadcast them by shuffles,
-// read row ends and split ids 32 rows at a time, and gather B rows through a 4-deep register
-// ring.  At 64 registers 8 CTAs (32 warps) fit on an SM; the gathers of many independent warps
-// hide the latency spread of a power-law column stream better than deeper rings in fewer warps.
+// one contiguous range of A and its rows are k0 .. kL themselves.  The lanes read column ids and
+// values 32 at a time, two batches ahead, into a 4-batch ring of (col, value) pairs in this warp's
+// shared memory (1 KB), which every step reads with one broadcast load; row ends and split ids
+// come 32 rows at a time; B rows are gathered through a 4-deep register ring.  At 64 registers
+// 8 CTAs (32 warps) fit on an SM: the gathers of many independent warps hide the latency spread
+// of a power-law column stream better than deeper rings in fewer warps.
 // ---------------------------------------------------------------------------------------------
 constexpr int kCRing = 4;
 
-template <int VPL, bool BF16, bool HINT>
+// FULL: every lane holds VPL whole vectors (K == 128 * VPL), so no per-lane width test
+template <int VPL, bool BF16, bool HINT, bool FULL>
 __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int lane, const Policies& pol,
-                                             float4* stash)
+                                             float4* park, int2* bat)
 {
     const int4 h0 = __ldg(reinterpret_cast<const int4*>(D.chunk_rec + c));
     const int4 h1 = __ldg(reinterpret_cast<const int4*>(D.chunk_rec + c) + 1);
@@ -687,22 +689,20 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
         if (lane == 0) atomicOr(D.status, kStatusInternal);  // guard: corrupt plan
         return;
     }
-    const int32_t* const colp = D.res_col + z0;
-    const float* const valp = D.res_val + z0;
     const int nv = D.K >> 2;
     constexpr int VB = BF16 ? 8 : 16;  // bytes of one 4-column vector
     const unsigned char* const Bl = reinterpret_cast<const unsigned char*>(D.B) + VB * lane;
     const uint32_t ldb_bytes = (uint32_t)(D.ldb * (BF16 ? 2 : 4));
 
-    // the last column id pads the ring past the chunk's end (value 0: a cached reload)
-    const int32_t clast = total > 0 ? ld_stream_i32<HINT>(colp + total - 1, pol.first) : 0;
-    auto batch = [&](int P0, int32_t& cc, float& vv) {
+    // ---- batches of 32 (col, value) pairs; past the end: the last column again with value 0 ----
+    const int32_t clast = total > 0 ? ld_stream_i32<HINT>(D.res_col + z0 + total - 1, pol.first) : 0;
+    auto fetch = [&](int P0, int32_t& cc, float& vv) {
         const int P = P0 + lane;
         cc = clast;
         vv = 0.f;
         if (P < total) {
-            cc = ld_stream_i32<HINT>(colp + P, pol.first);
-            vv = ld_stream_f32<HINT>(valp + P, pol.first);
+            cc = ld_stream_i32<HINT>(D.res_col + z0 + P, pol.first);
+            vv = ld_stream_f32<HINT>(D.res_val + z0 + P, pol.first);
         }
         if ((unsigned)cc >= (unsigned)D.n) {  // guard: never gather outside B
             atomicOr(D.status, kStatusInternal);
@@ -710,6 +710,15 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
             vv = 0.f;
         }
     };
+    auto put = [&](int P0, int32_t cc, float vv) { bat[(P0 & 127) + lane] = make_int2(cc, __float_as_int(vv)); };
+    int32_t cr;
+    float vr;
+    fetch(0, cr, vr);
+    put(0, cr, vr);
+    fetch(32, cr, vr);
+    put(32, cr, vr);
+    fetch(64, cr, vr);  // stored when batch 32 starts
+
     // lane j: stream end of row k0 + base + j (merge position of its end item, less b0 and the
     // end items of the rows before it) and its split id
     int32_t wend = 0x7fffffff, wsplit = -1;
@@ -722,29 +731,25 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
             wsplit = __ldg(D.row_split + k);
         }
     };
-
-    int32_t ca, cb, cn;
-    float va, vb, vn;
-    batch(0, ca, va);
-    batch(32, cb, vb);
     rows(0);
+    __syncwarp();
+
     float4 acc[VPL];
 #pragma unroll
     for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 b[kCRing][VPL];
     float w[kCRing];
-    auto gather = [&](int32_t col, float val, float4 (&dst)[VPL], float& wv) {
-        const unsigned char* row = Bl + (size_t)(uint32_t)col * ldb_bytes;
+    auto gather = [&](int2 e, float4 (&dst)[VPL], float& wv) {
+        const unsigned char* row = Bl + (size_t)(uint32_t)e.x * ldb_bytes;
 #pragma unroll
         for (int q = 0; q < VPL; ++q) {
-            if (lane + 32 * q < nv) dst[q] = ld_b4<BF16, HINT>(row + 32 * VB * q, 0, pol.last);
+            if (FULL || lane + 32 * q < nv) dst[q] = ld_b4<BF16, HINT>(row + 32 * VB * q, 0, pol.last);
             else dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        wv = val;
+        wv = __int_as_float(e.y);
     };
 #pragma unroll
-    for (int u = 0; u < kCRing; ++u)
-        gather(__shfl_sync(0xffffffffu, ca, u), __shfl_sync(0xffffffffu, va, u), b[u], w[u]);
+    for (int u = 0; u < kCRing; ++u) gather(bat[u], b[u], w[u]);
 
     // Row ends inside the stream.  Only the chunk's first and last rows can be split (a middle
     // row lies inside the chunk's merge range, so no other chunk touches it); the last one ends
@@ -753,6 +758,14 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     int r = 0;
     bool parked = false;
     int next_end = __shfl_sync(0xffffffffu, wend, 0);
+    auto store_row = [&]() {
+        float* crow = D.C + (int64_t)(k0 + r) * D.ldc;
+#pragma unroll
+        for (int q = 0; q < VPL; ++q) {
+            const int v = lane + 32 * q;
+            if (FULL || v < nv) st_c4<HINT>(crow + 4 * v, acc[q], pol.first);
+        }
+    };
     auto advance = [&]() {
 #pragma unroll
         for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -763,68 +776,59 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     auto flush = [&]() {  // inside the loop
         const int32_t sp = __shfl_sync(0xffffffffu, wsplit, r & 31);
         if (sp < 0) {
-            float* crow = D.C + (int64_t)(k0 + r) * D.ldc;
-#pragma unroll
-            for (int q = 0; q < VPL; ++q) {
-                const int v = lane + 32 * q;
-                if (v < nv) st_c4<HINT>(crow + 4 * v, acc[q], pol.first);
-            }
+            store_row();
         } else if (r == 0) {
 #pragma unroll
-            for (int q = 0; q < VPL; ++q) stash[32 * q + lane] = acc[q];
+            for (int q = 0; q < VPL; ++q) park[32 * q + lane] = acc[q];
             parked = true;
         } else if (lane == 0) {
             atomicOr(D.status, kStatusInternal);  // guard: a middle row marked split
         }
         advance();
     };
-    auto flush_last = [&]() {  // after the loop (any row, split or not)
-        const int32_t sp = __shfl_sync(0xffffffffu, wsplit, r & 31);
-        if (sp < 0) {
-            float* crow = D.C + (int64_t)(k0 + r) * D.ldc;
+    // one step: entry P (in the ring's slot u) accumulated, entry P + kCRing gathered into it
+    auto step = [&](int P, int u, const int2* e4) {
+        while (P >= next_end) flush();
 #pragma unroll
-            for (int q = 0; q < VPL; ++q) {
-                const int v = lane + 32 * q;
-                if (v < nv) st_c4<HINT>(crow + 4 * v, acc[q], pol.first);
-            }
-        } else {
-            deliver_split_row<VPL, HINT>(D, k0 + r, sp, c, acc[0], acc[VPL > 1 ? VPL - 1 : 0], lane, pol.first);
-        }
-        advance();
+        for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], b[u][q], acc[q]);
+        gather(e4[u], b[u], w[u]);
     };
 
-    for (int P0 = 0; P0 < total; P0 += 32) {
-        batch(P0 + 64, cn, vn);  // two batches ahead
-        for (int j0 = 0; j0 < 32; j0 += kCRing) {
-            if (P0 + j0 >= total) break;
-#pragma unroll
-            for (int u = 0; u < kCRing; ++u) {
-                const int P = P0 + j0 + u;
-                if (P >= total) break;  // past the last nonzero: later row ends belong after the loop
-                while (P >= next_end) flush();
-#pragma unroll
-                for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], b[u][q], acc[q]);
-                // entry P + kCRing: in this batch or the next (warp-uniform choice)
-                const int sl = j0 + u + kCRing;
-                const bool nx = sl >= 32;
-                const int32_t col = __shfl_sync(0xffffffffu, nx ? cb : ca, sl & 31);
-                const float val = __shfl_sync(0xffffffffu, nx ? vb : va, sl & 31);
-                gather(col, val, b[u], w[u]);
-            }
+    int P = 0;
+    for (; P + kCRing <= total; P += kCRing) {
+        if ((P & 31) == 0 && P > 0) {  // batch P + 32 into the ring, batch P + 64 requested
+            put(P + 32, cr, vr);
+            __syncwarp();
+            fetch(P + 64, cr, vr);
         }
-        ca = cb;
-        va = vb;
-        cb = cn;
-        vb = vn;
+        const int2* e4 = bat + ((P + kCRing) & 127);
+#pragma unroll
+        for (int u = 0; u < kCRing; ++u) step(P + u, u, e4);
+    }
+    if (P < total) {  // the last partial group (its batch is already in the ring)
+        if ((P & 31) == 0 && P > 0) {
+            put(P + 32, cr, vr);
+            __syncwarp();
+        }
+        const int2* e4 = bat + ((P + kCRing) & 127);
+#pragma unroll
+        for (int u = 0; u < kCRing; ++u)
+            if (P + u < total) step(P + u, u, e4);
     }
     if (parked) {
         float4 p[VPL];
 #pragma unroll
-        for (int q = 0; q < VPL; ++q) p[q] = stash[32 * q + lane];
+        for (int q = 0; q < VPL; ++q) p[q] = park[32 * q + lane];
         deliver_split_row<VPL, HINT>(D, k0, __ldg(D.row_split + k0), c, p[0], p[VPL > 1 ? VPL - 1 : 0], lane,
                                      pol.first);
     }
-    while (r < nr) flush_last();  // rows ending at or after the last nonzero (and the last row)
+    while (r < nr) {  // rows ending at or after the last nonzero (and the last row)
+        const int32_t sp = __shfl_sync(0xffffffffu, wsplit, r & 31);
+        if (sp < 0) store_row();
+        else deliver_split_row<VPL, HINT>(D, k0 + r, sp, c, acc[0], acc[VPL > 1 ? VPL - 1 : 0], lane, pol.first);
+        advance();
+    }
+    __syncwarp();  // the batch ring is reused by this warp's next chunk
 }
 
 template <int VPL, bool BF16, bool HINT>
@@ -834,8 +838,10 @@ __global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : 5) k_exec_contig(
     const __grid_constant__ ExecDesc d0)
 {
     __shared__ float4 s_park[kExecWarps * 32 * VPL];  // one parked partial row per warp
-    const int lane = threadIdx.x & 31;
-    float4* const park = s_park + (threadIdx.x >> 5) * 32 * VPL;
+    __shared__ int2 s_bat[kExecWarps * 128];          // per warp: 4 batches of 32 (col, value)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4* const park = s_park + warp * 32 * VPL;
+    int2* const bat = s_bat + warp * 128;
     Policies pol{0, 0};
     if (HINT) pol = make_policies();
     for (;;) {
@@ -853,7 +859,8 @@ __global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : 5) k_exec_contig(
             if (lane == 0) atomicOr(D.status, kStatusInternal);
             continue;
         }
-        contig_chunk<VPL, BF16, HINT>(D, (int32_t)c, lane, pol, park);
+        if (D.K == 128 * VPL) contig_chunk<VPL, BF16, HINT, true>(D, (int32_t)c, lane, pol, park, bat);
+        else contig_chunk<VPL, BF16, HINT, false>(D, (int32_t)c, lane, pol, park, bat);
     }
     // the last CTA out resets the tickets for the next launch (stream order makes it visible)
     __syncthreads();

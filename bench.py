@@ -105,6 +105,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM traffic of the execute kernel per launch: dram__bytes_read.sum + dram__bytes_write.sum
+# from one ncu capture (summarised in profiles/), keyed by workload and tune.  It is valid only for
+# the kernel source it was taken on: the digest of the execute kernel's sources must match,
+# otherwise the roofline reports traffic as null.
+EXEC_SOURCES = ("ns_exec.cu", "ns_internal.cuh", "ns_dense.cuh", "ns_ptx.cuh")
+MEASURED_TRAFFIC = {
+    # (workload, tau_tile, chunk_nnz, l2_hints): (source digest, bytes per launch)
+}
+
+
+def exec_source_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in EXEC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2606_22482_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, tune) -> float | None:
+    rec = MEASURED_TRAFFIC.get((workload, int(tune.tau_tile), int(tune.chunk_nnz), int(tune.l2_hints)))
+    if rec is None or rec[0] != exec_source_digest():
+        return None
+    return rec[1]
+
+
 def make_workload(name: str, seed: int):
     import synth
     if name == "powerlaw":
@@ -187,6 +213,7 @@ def main():
                     help="override the L2 policy of the tune (2: planner-marked hot B rows)")
     ap.add_argument("--tn", type=int, default=None, help="override the column-slice width TN")
     ap.add_argument("--chunk", type=int, default=None, help="override the residual chunk size W")
+    ap.add_argument("--tm", type=int, default=None, choices=[16, 32, 64], help="override the window height TM")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -273,6 +300,9 @@ def main():
     if args.tn is not None:
         tune.TN = args.tn
         tune_src += f", TN={args.tn}"
+    if args.tm is not None:
+        tune.TM = args.tm
+        tune_src += f", TM={args.tm}"
     if args.chunk is not None:
         tune.chunk_nnz = args.chunk
         tune.absorb_cap = args.chunk
@@ -359,7 +389,8 @@ def main():
                        step="device plan + one persistent execute launch", tune=tune.as_dict(),
                        tune_source=tune_src, plan=st),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm, "traffic": measured_traffic(args.workload, tune),
+                     "source_digest": exec_source_digest(),
                      "kernel": "k_exec (persistent execute)", "peak_source": f"{peak_src} hbm_gbs",
                      "algorithmic_bytes": alg_bytes, "n_touched": n_touched,
                      "kernel_ms": exec_ms, "frac_of_8000": achieved / 8000.0},

@@ -675,8 +675,10 @@ __global__ void __launch_bounds__(kExecThreads, DENSE ? 1 : 4) k_exec(const Exec
 // ---------------------------------------------------------------------------------------------
 constexpr int kCRing = 4;
 
-// FULL: every lane holds VPL whole vectors (K == 128 * VPL), so no per-lane width test
-template <int VPL, bool BF16, bool HINT, bool FULL>
+// FULL: every lane holds VPL whole vectors (K == 128 * VPL), so no per-lane width test.
+// HOT: the planner's hot-row map picks each gather's L2 policy; the map is read when a batch is
+// fetched and its bit travels as bit 31 of the column id.
+template <int VPL, bool BF16, bool HINT, bool FULL, bool HOT>
 __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int lane, const Policies& pol,
                                              float4* park, int2* bat)
 {
@@ -709,6 +711,7 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
             cc = 0;
             vv = 0.f;
         }
+        if (HOT) cc |= (int32_t)(((__ldg(D.hot + (cc >> 5)) >> (cc & 31)) & 1u) << 31);
     };
     auto put = [&](int P0, int32_t cc, float vv) { bat[(P0 & 127) + lane] = make_int2(cc, __float_as_int(vv)); };
     int32_t cr;
@@ -740,10 +743,12 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     float4 b[kCRing][VPL];
     float w[kCRing];
     auto gather = [&](int2 e, float4 (&dst)[VPL], float& wv) {
-        const unsigned char* row = Bl + (size_t)(uint32_t)e.x * ldb_bytes;
+        const uint32_t col = HOT ? ((uint32_t)e.x & 0x7fffffffu) : (uint32_t)e.x;
+        const unsigned char* row = Bl + (size_t)col * ldb_bytes;
+        const uint64_t pl = HOT ? (e.x < 0 ? pol.last : pol.first) : pol.last;
 #pragma unroll
         for (int q = 0; q < VPL; ++q) {
-            if (FULL || lane + 32 * q < nv) dst[q] = ld_b4<BF16, HINT>(row + 32 * VB * q, 0, pol.last);
+            if (FULL || lane + 32 * q < nv) dst[q] = ld_b4<BF16, HINT>(row + 32 * VB * q, 0, pl);
             else dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         wv = __int_as_float(e.y);
@@ -859,8 +864,14 @@ __global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : 5) k_exec_contig(
             if (lane == 0) atomicOr(D.status, kStatusInternal);
             continue;
         }
-        if (D.K == 128 * VPL) contig_chunk<VPL, BF16, HINT, true>(D, (int32_t)c, lane, pol, park, bat);
-        else contig_chunk<VPL, BF16, HINT, false>(D, (int32_t)c, lane, pol, park, bat);
+        const bool full = D.K == 128 * VPL;
+        if (HINT && D.hot) {
+            if (full) contig_chunk<VPL, BF16, HINT, true, HINT>(D, (int32_t)c, lane, pol, park, bat);
+            else contig_chunk<VPL, BF16, HINT, false, HINT>(D, (int32_t)c, lane, pol, park, bat);
+        } else {
+            if (full) contig_chunk<VPL, BF16, HINT, true, false>(D, (int32_t)c, lane, pol, park, bat);
+            else contig_chunk<VPL, BF16, HINT, false, false>(D, (int32_t)c, lane, pol, park, bat);
+        }
     }
     // the last CTA out resets the tickets for the next launch (stream order makes it visible)
     __syncthreads();

@@ -112,6 +112,8 @@ class ClockSampler:
 EXEC_SOURCES = ("ns_exec.cu", "ns_internal.cuh", "ns_dense.cuh", "ns_ptx.cuh")
 MEASURED_TRAFFIC = {
     # (workload, tau_tile, chunk_nnz, l2_hints): (source digest, bytes per launch)
+    ("powerlaw", 2147483647, 512, 1): ("fbb55f500ac67467", 1676301000 + 541267200),
+    ("powerlaw", 2147483647, 256, 1): ("fbb55f500ac67467", 1699082496 + 580894976),
 }
 
 

@@ -71,9 +71,21 @@ inline size_t dense_smem_bytes(int K, int TM, int TK, bool bf16)
     return (size_t)dense_geom(K, TM, TK, bf16).total;
 }
 
+// Opt the kernel in to the largest dynamic shared memory the device allows (never a per-plan
+// value: a smaller plan must not lower the limit under a larger plan's cached launches).
 inline ns_status_t dense_prepare(const void* kern, size_t smem)
 {
-    NS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, optin = 0;
+    NS_CUDA_TRY(cudaGetDevice(&dev));
+    NS_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    NS_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    if ((int64_t)smem > lim) {
+        set_error("execute needs %zu bytes of shared memory per block, the device allows %d", smem, lim);
+        return NS_ERR_UNSUPPORTED;
+    }
+    NS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     return NS_OK;
 }
 

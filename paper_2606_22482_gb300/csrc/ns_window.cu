@@ -25,6 +25,11 @@ namespace ns {
 constexpr int kWinThreads = 256;
 constexpr int kWinSmemKeys = 4096;  // windows up to this many elements sort in shared memory
 constexpr int kMaxTM = 64;
+// Windows with more elements than kWinSmemKeys, of a matrix with at most kDenseCols columns, count
+// their columns in a per-CTA array instead of sorting: byte counters (TM <= 64 < 256) packed four
+// to a word, then 16-bit ascending positions (U <= n < 65536), 3 bytes per column in all.
+constexpr int kDenseCols = 49152;
+constexpr int kEmitSmemWords = 4096;  // a window's dense-tile bitmaps assembled in shared memory
 
 // ---------------------------------------------------------------------------------------------
 // W1: kept rows
@@ -200,6 +205,8 @@ struct WinArgs {
     int32_t* win_ndv;
     int64_t* win_res;   // residual nonzeros of the window's rows
     int32_t* res_len;   // per row (m)
+    int32_t n;          // columns of A
+    int32_t count_cols; // 1: launched with 3 * round4(n) bytes of dynamic shared memory (n <= kDenseCols)
 };
 
 // row slot of window element e: the largest r < nrows with rb[r] <= e (empty rows share their
@@ -225,6 +232,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
     __shared__ int32_t binoff[kMaxTM + 1];
     __shared__ int32_t dcnt[kMaxTM];
     __shared__ int64_t s_carry[2];
+    __shared__ uint32_t tdense[kDenseCols / 16 / 32 + 1];  // counting path: dense flag per tile (TK >= 16)
 
     const int w = blockIdx.x;
     const int TM = a.TM, TK = a.TK;
@@ -239,37 +247,85 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
     for (int q = threadIdx.x; q < TM; q += blockDim.x) dcnt[q] = 0;
     __syncthreads();
 
-    // ---- sort the window's columns (merge of sorted row segments) ----
-    const bool in_smem = N <= kWinSmemKeys;
-    int32_t* b0 = in_smem ? skeys[0] : a.sortbuf0 + wbase;
-    int32_t* b1 = in_smem ? skeys[1] : a.sortbuf1 + wbase;
-    for (int64_t e = threadIdx.x; e < N; e += blockDim.x) b0[e] = a.ekey[wbase + e];
-    __syncthreads();
-    const int32_t* sorted = cta_merge_runs(b0, b1, N, rb, nrows);
-
-    // ---- run-length encode: ascending unique columns; start positions in upos (temp) ----
     int32_t* uasc = a.uasc + wbase;
     int32_t* ucnt = a.ucnt + wbase;
     int32_t* upos = a.upos + wbase;
-    if (threadIdx.x == 0) s_carry[0] = 0;
-    __syncthreads();
-    for (int64_t c0 = 0; c0 < N; c0 += blockDim.x) {
-        int64_t e = c0 + threadIdx.x;
-        int64_t f = (e < N && (e == 0 || sorted[e] != sorted[e - 1])) ? 1 : 0;
-        int64_t tot;
-        int64_t pre = block_excl_scan<int64_t, kWinThreads>(f, &tot, sscan) + s_carry[0];
-        if (f) {
-            uasc[pre] = sorted[e];
-            upos[pre] = (int32_t)e;
+    // ---- unique columns of the window in ascending order, with their counts ----
+    extern __shared__ uint32_t dyn_cols[];
+    const bool count_cols = a.count_cols && N > kWinSmemKeys;  // window-uniform
+    const int nwords = (a.n + 3) >> 2;
+    uint16_t* const cpos = reinterpret_cast<uint16_t*>(dyn_cols + nwords);  // column -> ascending index
+    if (count_cols) {
+        // byte counters, four per word (a count is at most TM <= 64)
+        for (int q = threadIdx.x; q < nwords; q += blockDim.x) dyn_cols[q] = 0u;
+        __syncthreads();
+        for (int64_t e0 = threadIdx.x; e0 < N; e0 += 8 * blockDim.x) {
+            int32_t cv[8];  // eight column ids per thread in flight
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t e = e0 + (int64_t)u * blockDim.x;
+                cv[u] = e < N ? a.ekey[wbase + e] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (cv[u] >= 0) atomicAdd(&dyn_cols[cv[u] >> 2], 1u << (8 * (cv[u] & 3)));
         }
+        if (threadIdx.x == 0) s_carry[0] = 0;
         __syncthreads();
-        if (threadIdx.x == 0) s_carry[0] += tot;
+        // compaction in ascending column order
+        for (int q0 = 0; q0 < nwords; q0 += blockDim.x) {
+            const int q = q0 + threadIdx.x;
+            const uint32_t wv = q < nwords ? dyn_cols[q] : 0u;
+            int64_t f = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) f += ((wv >> (8 * b)) & 0xffu) ? 1 : 0;
+            int64_t tot;
+            int64_t pre = block_excl_scan<int64_t, kWinThreads>(f, &tot, sscan) + s_carry[0];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t cnt = (wv >> (8 * b)) & 0xffu;
+                if (cnt) {
+                    uasc[pre] = 4 * q + b;
+                    ucnt[pre] = (int32_t)cnt;
+                    cpos[4 * q + b] = (uint16_t)pre;
+                    ++pre;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) s_carry[0] += tot;
+            __syncthreads();
+        }
+    } else {
+        // sort the window's columns (merge of sorted row segments), then run-length encode;
+        // start positions go to upos (temporary)
+        const bool in_smem = N <= kWinSmemKeys;
+        int32_t* b0 = in_smem ? skeys[0] : a.sortbuf0 + wbase;
+        int32_t* b1 = in_smem ? skeys[1] : a.sortbuf1 + wbase;
+        for (int64_t e = threadIdx.x; e < N; e += blockDim.x) b0[e] = a.ekey[wbase + e];
         __syncthreads();
+        const int32_t* sorted = cta_merge_runs(b0, b1, N, rb, nrows);
+        if (threadIdx.x == 0) s_carry[0] = 0;
+        __syncthreads();
+        for (int64_t c0 = 0; c0 < N; c0 += blockDim.x) {
+            int64_t e = c0 + threadIdx.x;
+            int64_t f = (e < N && (e == 0 || sorted[e] != sorted[e - 1])) ? 1 : 0;
+            int64_t tot;
+            int64_t pre = block_excl_scan<int64_t, kWinThreads>(f, &tot, sscan) + s_carry[0];
+            if (f) {
+                uasc[pre] = sorted[e];
+                upos[pre] = (int32_t)e;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) s_carry[0] += tot;
+            __syncthreads();
+        }
     }
     const int64_t U = s_carry[0];
-    for (int64_t u = threadIdx.x; u < U; u += blockDim.x) {
-        int64_t nxt = u + 1 < U ? upos[u + 1] : N;
-        ucnt[u] = (int32_t)(nxt - upos[u]);
+    if (!count_cols) {
+        for (int64_t u = threadIdx.x; u < U; u += blockDim.x) {
+            int64_t nxt = u + 1 < U ? upos[u + 1] : N;
+            ucnt[u] = (int32_t)(nxt - upos[u]);
+        }
     }
     __syncthreads();
 
@@ -327,6 +383,13 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
     }
     __syncthreads();
 
+    // counting path: the column table now maps a column to its canonical position
+    if (count_cols) {
+        for (int64_t u = threadIdx.x; u < U; u += blockDim.x) cpos[uasc[u]] = (uint16_t)upos[u];
+        for (int q = threadIdx.x; q < kDenseCols / 16 / 32 + 1; q += blockDim.x) tdense[q] = 0u;
+        __syncthreads();
+    }
+
     // ---- tiles: nnz, density, dense rank and value offset inside the window ----
     const int64_t ntile = (U + TK - 1) / TK;
     int32_t* trank = a.trank + wbase;
@@ -346,6 +409,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
         if (t < ntile) {
             trank[t] = v ? (int32_t)(s_carry[0] + (pre >> 32)) : -1;
             tvoff[t] = (int32_t)(s_carry[1] + (pre & 0xffffffffLL));
+            if (count_cols && v) atomicOr(&tdense[t >> 5], 1u << (t & 31));
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -357,17 +421,51 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
 
     // ---- elements: compacted position, dense counts per row ----
     int32_t* epos = a.epos + wbase;
-    for (int64_t e = threadIdx.x; e < N; e += blockDim.x) {
+    if (count_cols) {
+        // table lookups only; eight column ids per thread in flight
+        constexpr int kU = 8;
+        for (int64_t e0 = threadIdx.x; e0 - threadIdx.x < N; e0 += kU * blockDim.x) {
+            int32_t cv[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t e = e0 + (int64_t)u * blockDim.x;
+                cv[u] = e < N ? a.ekey[wbase + e] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t e = e0 + (int64_t)u * blockDim.x;
+                int slot = -1;
+                if (cv[u] >= 0) {
+                    const int32_t pos = cpos[cv[u]];
+                    epos[e] = pos;
+                    const int t = pos / TK;
+                    if ((tdense[t >> 5] >> (t & 31)) & 1u) slot = row_slot_of(rb0, nrows, e);
+                }
+                // dense elements per row: one shared atomic per distinct row among the warp's lanes
+                const unsigned peers = __match_any_sync(0xffffffffu, slot);
+                if (slot >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&dcnt[slot], __popc(peers));
+            }
+        }
+    }
+    for (int64_t e = count_cols ? N : threadIdx.x; e < N; e += blockDim.x) {
         const int32_t col = a.ekey[wbase + e];
-        int64_t lo = 0, hi = U;  // lower bound of col in uasc
-        while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
-            if (uasc[mid] < col) lo = mid + 1;
-            else hi = mid;
+        int64_t lo = 0, hi = U;  // ascending index of col: the counters' table, or a lower bound in uasc
+        if (count_cols) {
+            lo = cpos[col];
+        } else {
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if (uasc[mid] < col) lo = mid + 1;
+                else hi = mid;
+            }
         }
         const int32_t pos = upos[lo];
         epos[e] = pos;
-        if (trank[pos / TK] >= 0) atomicAdd(&dcnt[row_slot_of(rb0, nrows, e)], 1);
+        // dense elements per row: one shared atomic per distinct row of the warp's 32 elements
+        const int slot = trank[pos / TK] >= 0 ? row_slot_of(rb0, nrows, e) : -1;
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, slot);
+        if (slot >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&dcnt[slot], __popc(peers));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -521,39 +619,88 @@ __global__ void __launch_bounds__(kWinThreads) k_emit_tiles(EmitArgs a)
         }
         a.dtile_voff[d] = (int32_t)(a.win_vbase[w] + a.tvoff[wbase + t]);
     }
-    // bitmap bits
-    for (int64_t e = threadIdx.x; e < N; e += blockDim.x) {
-        int32_t pos = a.epos[wbase + e];
-        int32_t k = a.trank[wbase + pos / TK];
-        if (k < 0) continue;
-        int r = row_slot_of(rb0, nrows, e);
-        int bit = r * TK + pos % TK;
-        atomicOr(a.dtile_bits + (int64_t)(dbase + k) * BW + bit / 32, 1u << (bit % 32));
+    // bitmap bits: in shared memory when the window's dense tiles fit (then copied out), else
+    // straight into the plan with global atomics
+    __shared__ uint32_t sbits[kEmitSmemWords];
+    __shared__ int32_t wpre[kEmitSmemWords];
+    const int32_t ndt = a.win_ndt[w];
+    const bool in_smem = (int64_t)ndt * BW <= kEmitSmemWords;
+    if (in_smem) {
+        for (int q = threadIdx.x; q < ndt * BW; q += blockDim.x) sbits[q] = 0u;
+        __syncthreads();
+    }
+    constexpr int kU = 4;  // elements per thread in flight
+    for (int64_t e0 = threadIdx.x; e0 < N; e0 += kU * blockDim.x) {
+        int32_t pv[kU], kv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t e = e0 + (int64_t)u * blockDim.x;
+            pv[u] = e < N ? a.epos[wbase + e] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) kv[u] = pv[u] >= 0 ? a.trank[wbase + pv[u] / TK] : -1;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (kv[u] < 0) continue;
+            const int64_t e = e0 + (int64_t)u * blockDim.x;
+            const int r = row_slot_of(rb0, nrows, e);
+            const int bit = r * TK + pv[u] % TK;
+            if (in_smem) atomicOr(&sbits[kv[u] * BW + bit / 32], 1u << (bit % 32));
+            else atomicOr(a.dtile_bits + (int64_t)(dbase + kv[u]) * BW + bit / 32, 1u << (bit % 32));
+        }
     }
     __syncthreads();
-    // packed values in bitmap order
-    for (int64_t e = threadIdx.x; e < N; e += blockDim.x) {
-        int32_t pos = a.epos[wbase + e];
-        int32_t t = pos / TK;
-        int32_t k = a.trank[wbase + t];
-        if (k < 0) continue;
-        int64_t d = dbase + k;
-        int r = row_slot_of(rb0, nrows, e);
-        int bit = r * TK + pos % TK;
-        const uint32_t* bw = a.dtile_bits + d * BW;
-        int idx = 0;
-        for (int q = 0; q < bit / 32; ++q) idx += __popc(__ldcg(bw + q));
-        idx += __popc(__ldcg(bw + bit / 32) & ((1u << (bit % 32)) - 1u));
-        int64_t vi = (int64_t)a.win_vbase[w] + a.tvoff[wbase + t] + idx;
-        int32_t p = a.eidx[wbase + e];
-        float v = __ldg(a.vals + p);
-        if (a.bf16) {
-            __nv_bfloat16 h = __float2bfloat16_rn(v);
-            reinterpret_cast<uint16_t*>(a.dtile_vals)[vi] = *reinterpret_cast<uint16_t*>(&h);
-        } else {
-            reinterpret_cast<float*>(a.dtile_vals)[vi] = v;
+    // per dense tile, the value index of each bitmap word's first bit (shared memory when the
+    // window's dense tiles fit, else summed per element below)
+    if (in_smem) {
+        for (int q = threadIdx.x; q < ndt * BW; q += blockDim.x) a.dtile_bits[(int64_t)dbase * BW + q] = sbits[q];
+        for (int k = threadIdx.x; k < ndt; k += blockDim.x) {
+            int acc = 0;
+            for (int q = 0; q < BW; ++q) {
+                wpre[k * BW + q] = acc;
+                acc += __popc(sbits[k * BW + q]);
+            }
         }
-        a.pdense[p] = 1;
+        __syncthreads();
+    }
+    // packed values in bitmap order
+    for (int64_t e0 = threadIdx.x; e0 < N; e0 += kU * blockDim.x) {
+        int32_t pv[kU], kv[kU], iv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t e = e0 + (int64_t)u * blockDim.x;
+            pv[u] = e < N ? a.epos[wbase + e] : -1;
+            iv[u] = e < N ? a.eidx[wbase + e] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) kv[u] = pv[u] >= 0 ? a.trank[wbase + pv[u] / TK] : -1;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (kv[u] < 0) continue;
+            const int64_t e = e0 + (int64_t)u * blockDim.x;
+            const int32_t t = pv[u] / TK;
+            const int64_t d = dbase + kv[u];
+            const int r = row_slot_of(rb0, nrows, e);
+            const int bit = r * TK + pv[u] % TK;
+            int idx = 0;
+            if (in_smem) {
+                idx = wpre[kv[u] * BW + bit / 32] + __popc(sbits[kv[u] * BW + bit / 32] & ((1u << (bit % 32)) - 1u));
+            } else {
+                const uint32_t* bw = a.dtile_bits + d * BW;
+                for (int q = 0; q < bit / 32; ++q) idx += __popc(__ldcg(bw + q));
+                idx += __popc(__ldcg(bw + bit / 32) & ((1u << (bit % 32)) - 1u));
+            }
+            const int64_t vi = (int64_t)a.win_vbase[w] + a.tvoff[wbase + t] + idx;
+            const int32_t p = iv[u];
+            const float v = __ldg(a.vals + p);
+            if (a.bf16) {
+                __nv_bfloat16 h = __float2bfloat16_rn(v);
+                reinterpret_cast<uint16_t*>(a.dtile_vals)[vi] = *reinterpret_cast<uint16_t*>(&h);
+            } else {
+                reinterpret_cast<float*>(a.dtile_vals)[vi] = v;
+            }
+            a.pdense[p] = 1;
+        }
     }
 }
 
@@ -695,10 +842,17 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
     k_res_len_free_rows<<<wgrid(m), 256, 0, s>>>(P->rowptr, m, t.tau_row, res_len);
     NS_LAUNCH_CHECK();
     if (n_win > 0) {
+        const bool count_cols = n <= kDenseCols;
         WinArgs wa{P->rowptr, aic_rows, row_kbase, ekey, m_aic, TM, TK, t.tau_tile, t.col_order,
                    sb0, sb1, uasc, ucnt, upos, ucan, ccnt, trank, tvoff, epos,
-                   win_U, win_ndt, win_ndv, win_res, res_len};
-        k_window_compact<<<(unsigned)n_win, kWinThreads, 0, s>>>(wa);
+                   win_U, win_ndt, win_ndv, win_res, res_len, (int32_t)n, count_cols ? 1 : 0};
+        const size_t dyn = count_cols ? (size_t)3 * (((n + 3) / 4) * 4) : 0;
+        // static + dynamic shared memory above 48 KB needs the opt-in; one fixed limit (the largest
+        // counting table) keeps concurrent planners from lowering it under each other's launches
+        if (dyn > 0)
+            NS_CUDA_TRY(cudaFuncSetAttribute(k_window_compact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             3 * kDenseCols));
+        k_window_compact<<<(unsigned)n_win, kWinThreads, dyn, s>>>(wa);
         NS_LAUNCH_CHECK();
     }
 

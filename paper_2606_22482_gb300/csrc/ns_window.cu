@@ -22,7 +22,7 @@
 
 namespace ns {
 
-constexpr int kWinThreads = 256;
+constexpr int kWinThreads = 512;
 constexpr int kWinSmemKeys = 4096;  // windows up to this many elements sort in shared memory
 constexpr int kMaxTM = 64;
 // Windows with more elements than kWinSmemKeys, of a matrix with at most kDenseCols columns, count
@@ -30,6 +30,7 @@ constexpr int kMaxTM = 64;
 // to a word, then 16-bit ascending positions (U <= n < 65536), 3 bytes per column in all.
 constexpr int kDenseCols = 49152;
 constexpr int kEmitSmemWords = 4096;  // a window's dense-tile bitmaps assembled in shared memory
+constexpr int kEmitSmemTiles = 4096;  // and its tiles' dense ranks
 
 // ---------------------------------------------------------------------------------------------
 // W1: kept rows
@@ -422,29 +423,31 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
     // ---- elements: compacted position, dense counts per row ----
     int32_t* epos = a.epos + wbase;
     if (count_cols) {
-        // table lookups only; eight column ids per thread in flight
-        constexpr int kU = 8;
-        for (int64_t e0 = threadIdx.x; e0 - threadIdx.x < N; e0 += kU * blockDim.x) {
-            int32_t cv[kU];
+        // table lookups only, one warp per row: the row's dense elements counted by ballots
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        for (int r = warp; r < nrows; r += nwarps) {
+            int cnt = 0;
+            const int64_t rend = rb0[r + 1];
+            for (int64_t eb = rb0[r]; eb < rend; eb += 128) {  // four column ids per lane in flight
+                int32_t cv[4];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int64_t e = e0 + (int64_t)u * blockDim.x;
-                cv[u] = e < N ? a.ekey[wbase + e] : -1;
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int64_t e = e0 + (int64_t)u * blockDim.x;
-                int slot = -1;
-                if (cv[u] >= 0) {
-                    const int32_t pos = cpos[cv[u]];
-                    epos[e] = pos;
-                    const int t = pos / TK;
-                    if ((tdense[t >> 5] >> (t & 31)) & 1u) slot = row_slot_of(rb0, nrows, e);
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t e = eb + 32 * u + lane;
+                    cv[u] = e < rend ? a.ekey[wbase + e] : -1;
                 }
-                // dense elements per row: one shared atomic per distinct row among the warp's lanes
-                const unsigned peers = __match_any_sync(0xffffffffu, slot);
-                if (slot >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&dcnt[slot], __popc(peers));
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    bool dense = false;
+                    if (cv[u] >= 0) {
+                        const int32_t pos = cpos[cv[u]];
+                        epos[eb + 32 * u + lane] = pos;
+                        const int t = pos / TK;
+                        dense = (tdense[t >> 5] >> (t & 31)) & 1u;
+                    }
+                    cnt += __popc(__ballot_sync(0xffffffffu, dense));
+                }
             }
+            if (lane == 0) dcnt[r] += cnt;
         }
     }
     for (int64_t e = count_cols ? N : threadIdx.x; e < N; e += blockDim.x) {
@@ -596,21 +599,28 @@ struct EmitArgs {
 __global__ void __launch_bounds__(kWinThreads) k_emit_tiles(EmitArgs a)
 {
     __shared__ int64_t rb0[kMaxTM + 1];
+    __shared__ uint32_t sbits[kEmitSmemWords];
+    __shared__ int32_t wpre[kEmitSmemWords];
+    __shared__ int16_t srank[kEmitSmemTiles];
     const int w = blockIdx.x;
     if (a.win_ndt[w] == 0) return;
     const int TM = a.TM, TK = a.TK, BW = TM * TK / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int64_t r0 = (int64_t)w * TM;
     const int nrows = (int)(a.m_aic - r0 < TM ? a.m_aic - r0 : TM);
     const int64_t wbase = a.row_kbase[r0];
-    const int64_t N = a.row_kbase[r0 + nrows] - wbase;
     for (int q = threadIdx.x; q <= nrows; q += blockDim.x) rb0[q] = a.row_kbase[r0 + q] - wbase;
-    __syncthreads();
     const int64_t U = a.win_U[w];
     const int64_t ntile = (U + TK - 1) / TK;
     const int32_t dbase = a.win_dptr[w];
+    const int32_t ndt = a.win_ndt[w];
+    // the window's dense-tile bitmaps (and tile ranks) in shared memory when they fit, else the
+    // plan's bitmaps with global atomics and the ranks from global memory
+    const bool in_smem = (int64_t)ndt * BW <= kEmitSmemWords && ntile <= kEmitSmemTiles;
     // columns and value offsets of the dense tiles
     for (int64_t t = threadIdx.x; t < ntile; t += blockDim.x) {
         int32_t k = a.trank[wbase + t];
+        if (in_smem) srank[t] = (int16_t)k;
         if (k < 0) continue;
         int64_t d = dbase + k;
         for (int c = 0; c < TK; ++c) {
@@ -619,39 +629,35 @@ __global__ void __launch_bounds__(kWinThreads) k_emit_tiles(EmitArgs a)
         }
         a.dtile_voff[d] = (int32_t)(a.win_vbase[w] + a.tvoff[wbase + t]);
     }
-    // bitmap bits: in shared memory when the window's dense tiles fit (then copied out), else
-    // straight into the plan with global atomics
-    __shared__ uint32_t sbits[kEmitSmemWords];
-    __shared__ int32_t wpre[kEmitSmemWords];
-    const int32_t ndt = a.win_ndt[w];
-    const bool in_smem = (int64_t)ndt * BW <= kEmitSmemWords;
-    if (in_smem) {
+    if (in_smem)
         for (int q = threadIdx.x; q < ndt * BW; q += blockDim.x) sbits[q] = 0u;
-        __syncthreads();
-    }
-    constexpr int kU = 4;  // elements per thread in flight
-    for (int64_t e0 = threadIdx.x; e0 < N; e0 += kU * blockDim.x) {
-        int32_t pv[kU], kv[kU];
+    __syncthreads();
+    auto rank_of = [&](int32_t pos) -> int32_t {
+        return in_smem ? (int32_t)srank[pos / TK] : a.trank[wbase + pos / TK];
+    };
+    // bitmap bits: one warp per row of the window (the row of an element is its warp's row)
+    for (int r = warp; r < nrows; r += nwarps) {
+        const int64_t rend = rb0[r + 1];
+        for (int64_t eb = rb0[r]; eb < rend; eb += 128) {  // four positions per lane in flight
+            int32_t pv[4];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int64_t e = e0 + (int64_t)u * blockDim.x;
-            pv[u] = e < N ? a.epos[wbase + e] : -1;
-        }
+            for (int u = 0; u < 4; ++u) {
+                const int64_t e = eb + 32 * u + lane;
+                pv[u] = e < rend ? a.epos[wbase + e] : -1;
+            }
 #pragma unroll
-        for (int u = 0; u < kU; ++u) kv[u] = pv[u] >= 0 ? a.trank[wbase + pv[u] / TK] : -1;
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            if (kv[u] < 0) continue;
-            const int64_t e = e0 + (int64_t)u * blockDim.x;
-            const int r = row_slot_of(rb0, nrows, e);
-            const int bit = r * TK + pv[u] % TK;
-            if (in_smem) atomicOr(&sbits[kv[u] * BW + bit / 32], 1u << (bit % 32));
-            else atomicOr(a.dtile_bits + (int64_t)(dbase + kv[u]) * BW + bit / 32, 1u << (bit % 32));
+            for (int u = 0; u < 4; ++u) {
+                if (pv[u] < 0) continue;
+                const int32_t k = rank_of(pv[u]);
+                if (k < 0) continue;
+                const int bit = r * TK + pv[u] % TK;
+                if (in_smem) atomicOr(&sbits[k * BW + bit / 32], 1u << (bit % 32));
+                else atomicOr(a.dtile_bits + (int64_t)(dbase + k) * BW + bit / 32, 1u << (bit % 32));
+            }
         }
     }
     __syncthreads();
-    // per dense tile, the value index of each bitmap word's first bit (shared memory when the
-    // window's dense tiles fit, else summed per element below)
+    // per dense tile, the value index of each bitmap word's first bit
     if (in_smem) {
         for (int q = threadIdx.x; q < ndt * BW; q += blockDim.x) a.dtile_bits[(int64_t)dbase * BW + q] = sbits[q];
         for (int k = threadIdx.x; k < ndt; k += blockDim.x) {
@@ -664,34 +670,35 @@ __global__ void __launch_bounds__(kWinThreads) k_emit_tiles(EmitArgs a)
         __syncthreads();
     }
     // packed values in bitmap order
-    for (int64_t e0 = threadIdx.x; e0 < N; e0 += kU * blockDim.x) {
-        int32_t pv[kU], kv[kU], iv[kU];
+    const int64_t vbase = a.win_vbase[w];
+    for (int r = warp; r < nrows; r += nwarps) {
+        const int64_t rend = rb0[r + 1];
+        for (int64_t eb = rb0[r]; eb < rend; eb += 128) {
+          int32_t pv[4], iv[4];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int64_t e = e0 + (int64_t)u * blockDim.x;
-            pv[u] = e < N ? a.epos[wbase + e] : -1;
-            iv[u] = e < N ? a.eidx[wbase + e] : -1;
-        }
+          for (int u = 0; u < 4; ++u) {
+              const int64_t e = eb + 32 * u + lane;
+              pv[u] = e < rend ? a.epos[wbase + e] : -1;
+              iv[u] = e < rend ? a.eidx[wbase + e] : -1;
+          }
 #pragma unroll
-        for (int u = 0; u < kU; ++u) kv[u] = pv[u] >= 0 ? a.trank[wbase + pv[u] / TK] : -1;
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            if (kv[u] < 0) continue;
-            const int64_t e = e0 + (int64_t)u * blockDim.x;
-            const int32_t t = pv[u] / TK;
-            const int64_t d = dbase + kv[u];
-            const int r = row_slot_of(rb0, nrows, e);
-            const int bit = r * TK + pv[u] % TK;
+          for (int u = 0; u < 4; ++u) {
+            const int32_t pos = pv[u];
+            const int32_t p = iv[u];
+            if (pos < 0) continue;
+            const int32_t k = rank_of(pos);
+            if (k < 0) continue;
+            const int32_t t = pos / TK;
+            const int bit = r * TK + pos % TK;
             int idx = 0;
             if (in_smem) {
-                idx = wpre[kv[u] * BW + bit / 32] + __popc(sbits[kv[u] * BW + bit / 32] & ((1u << (bit % 32)) - 1u));
+                idx = wpre[k * BW + bit / 32] + __popc(sbits[k * BW + bit / 32] & ((1u << (bit % 32)) - 1u));
             } else {
-                const uint32_t* bw = a.dtile_bits + d * BW;
+                const uint32_t* bw = a.dtile_bits + (int64_t)(dbase + k) * BW;
                 for (int q = 0; q < bit / 32; ++q) idx += __popc(__ldcg(bw + q));
                 idx += __popc(__ldcg(bw + bit / 32) & ((1u << (bit % 32)) - 1u));
             }
-            const int64_t vi = (int64_t)a.win_vbase[w] + a.tvoff[wbase + t] + idx;
-            const int32_t p = iv[u];
+            const int64_t vi = vbase + a.tvoff[wbase + t] + idx;
             const float v = __ldg(a.vals + p);
             if (a.bf16) {
                 __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -700,6 +707,7 @@ __global__ void __launch_bounds__(kWinThreads) k_emit_tiles(EmitArgs a)
                 reinterpret_cast<float*>(a.dtile_vals)[vi] = v;
             }
             a.pdense[p] = 1;
+          }
         }
     }
 }

@@ -16,6 +16,8 @@
 //
 // L2 policy (Section 6.2.1 hot-B staging in GPU form): A's arrays and C are streamed with an
 // evict-first policy, B rows are loaded with evict-last so that reused B rows stay in L2.
+#include <type_traits>
+
 #include "ns_internal.cuh"
 #include "ns_ptx.cuh"
 
@@ -675,13 +677,19 @@ __global__ void __launch_bounds__(kExecThreads, DENSE ? 1 : 4) k_exec(const Exec
 // ---------------------------------------------------------------------------------------------
 constexpr int kCRing = 4;
 
-// FULL: every lane holds VPL whole vectors (K == 128 * VPL), so no per-lane width test.
+// EPS: nonzeros per warp step (Section 7 "vector tiles merging"): the warp splits into EPS lane
+// groups of G = 32 / EPS lanes, group g takes entry P + g of the step, and a row's partial sums
+// are added across the groups when the row ends (K <= 4 G, so VPL = 1 when EPS > 1).
+// FULL: every lane of a group holds VPL whole vectors (K == 4 G VPL), so no per-lane width test.
 // HOT: the planner's hot-row map picks each gather's L2 policy; the map is read when a batch is
 // fetched and its bit travels as bit 31 of the column id.
-template <int VPL, bool BF16, bool HINT, bool FULL, bool HOT>
+template <int VPL, int EPS, bool BF16, bool HINT, bool FULL, bool HOT>
 __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int lane, const Policies& pol,
                                              float4* park, int2* bat)
 {
+    static_assert(EPS == 1 || VPL == 1, "several nonzeros per step only for K <= 128");
+    constexpr int G = 32 / EPS;
+    const int g = lane / G, li = lane % G;
     const int4 h0 = __ldg(reinterpret_cast<const int4*>(D.chunk_rec + c));
     const int4 h1 = __ldg(reinterpret_cast<const int4*>(D.chunk_rec + c) + 1);
     const int32_t b0 = h0.x, k0 = h0.z, kL = h0.w, z0 = h1.x, total = h1.y;
@@ -693,7 +701,7 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     }
     const int nv = D.K >> 2;
     constexpr int VB = BF16 ? 8 : 16;  // bytes of one 4-column vector
-    const unsigned char* const Bl = reinterpret_cast<const unsigned char*>(D.B) + VB * lane;
+    const unsigned char* const Bl = reinterpret_cast<const unsigned char*>(D.B) + VB * li;
     const uint32_t ldb_bytes = (uint32_t)(D.ldb * (BF16 ? 2 : 4));
 
     // ---- batches of 32 (col, value) pairs; past the end: the last column again with value 0 ----
@@ -748,13 +756,14 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
         const uint64_t pl = HOT ? (e.x < 0 ? pol.last : pol.first) : pol.last;
 #pragma unroll
         for (int q = 0; q < VPL; ++q) {
-            if (FULL || lane + 32 * q < nv) dst[q] = ld_b4<BF16, HINT>(row + 32 * VB * q, 0, pl);
+            if (FULL || li + 32 * q < nv) dst[q] = ld_b4<BF16, HINT>(row + 32 * VB * q, 0, pl);
             else dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         wv = __int_as_float(e.y);
     };
+    // step u of a group covers entries P + u EPS + g; the ring's first four steps
 #pragma unroll
-    for (int u = 0; u < kCRing; ++u) gather(bat[u], b[u], w[u]);
+    for (int u = 0; u < kCRing; ++u) gather(bat[u * EPS + g], b[u], w[u]);
 
     // Row ends inside the stream.  Only the chunk's first and last rows can be split (a middle
     // row lies inside the chunk's merge range, so no other chunk touches it); the last one ends
@@ -763,12 +772,23 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     int r = 0;
     bool parked = false;
     int next_end = __shfl_sync(0xffffffffu, wend, 0);
-    auto store_row = [&]() {
+    auto reduce_groups = [&]() {  // every group ends up with the row's full sum
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1)
+#pragma unroll
+            for (int q = 0; q < VPL; ++q) {
+                acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, o);
+                acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, o);
+                acc[q].z += __shfl_xor_sync(0xffffffffu, acc[q].z, o);
+                acc[q].w += __shfl_xor_sync(0xffffffffu, acc[q].w, o);
+            }
+    };
+    auto store_row = [&]() {  // group 0 stores
         float* crow = D.C + (int64_t)(k0 + r) * D.ldc;
 #pragma unroll
         for (int q = 0; q < VPL; ++q) {
-            const int v = lane + 32 * q;
-            if (FULL || v < nv) st_c4<HINT>(crow + 4 * v, acc[q], pol.first);
+            const int v = li + 32 * q;
+            if (g == 0 && (FULL || v < nv)) st_c4<HINT>(crow + 4 * v, acc[q], pol.first);
         }
     };
     auto advance = [&]() {
@@ -780,6 +800,7 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     };
     auto flush = [&]() {  // inside the loop
         const int32_t sp = __shfl_sync(0xffffffffu, wsplit, r & 31);
+        if (EPS > 1) reduce_groups();
         if (sp < 0) {
             store_row();
         } else if (r == 0) {
@@ -791,34 +812,57 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
         }
         advance();
     };
-    // one step: entry P (in the ring's slot u) accumulated, entry P + kCRing gathered into it
-    auto step = [&](int P, int u, const int2* e4) {
-        while (P >= next_end) flush();
+    // One step: entries P .. P + EPS - 1 (ring slot u) accumulated, then the slot gathers the
+    // entries kCRing steps ahead.  A row that ends inside the step takes the groups before its end;
+    // rows ending at or after the chunk's last nonzero are left to the end.  TAIL: the step may
+    // reach past the last nonzero (those groups add nothing).
+    auto step = [&](int P, int u, const int2* e1, auto tail) {
+        constexpr bool TAIL = decltype(tail)::value;
+        const int mine = P + g;
+        if (next_end >= P + EPS || next_end >= total) {
+            if (!TAIL || mine < total) {
 #pragma unroll
-        for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], b[u][q], acc[q]);
-        gather(e4[u], b[u], w[u]);
+                for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], b[u][q], acc[q]);
+            }
+        } else {
+            int from = P;
+            while (next_end < P + EPS && next_end < total) {
+                if (mine >= from && mine < next_end) {
+#pragma unroll
+                    for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], b[u][q], acc[q]);
+                }
+                if (next_end > from) from = next_end;
+                flush();
+            }
+            if (mine >= from && (!TAIL || mine < total)) {
+#pragma unroll
+                for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], b[u][q], acc[q]);
+            }
+        }
+        gather(e1[u * EPS + g], b[u], w[u]);
     };
 
+    constexpr int GS = kCRing * EPS;  // entries per group of steps (divides the batch of 32)
     int P = 0;
-    for (; P + kCRing <= total; P += kCRing) {
+    for (; P + GS <= total; P += GS) {
         if ((P & 31) == 0 && P > 0) {  // batch P + 32 into the ring, batch P + 64 requested
             put(P + 32, cr, vr);
             __syncwarp();
             fetch(P + 64, cr, vr);
         }
-        const int2* e4 = bat + ((P + kCRing) & 127);
+        const int2* e1 = bat + ((P + GS) & 127);  // entries P + GS .. P + 2 GS - 1 (GS divides 128)
 #pragma unroll
-        for (int u = 0; u < kCRing; ++u) step(P + u, u, e4);
+        for (int u = 0; u < kCRing; ++u) step(P + u * EPS, u, e1, std::false_type{});
     }
-    if (P < total) {  // the last partial group (its batch is already in the ring)
+    if (P < total) {  // the last partial group (its entries are already in the ring)
         if ((P & 31) == 0 && P > 0) {
             put(P + 32, cr, vr);
             __syncwarp();
         }
-        const int2* e4 = bat + ((P + kCRing) & 127);
+        const int2* e1 = bat + ((P + GS) & 127);
 #pragma unroll
         for (int u = 0; u < kCRing; ++u)
-            if (P + u < total) step(P + u, u, e4);
+            if (P + u * EPS < total) step(P + u * EPS, u, e1, std::true_type{});
     }
     if (parked) {
         float4 p[VPL];
@@ -829,6 +873,7 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     }
     while (r < nr) {  // rows ending at or after the last nonzero (and the last row)
         const int32_t sp = __shfl_sync(0xffffffffu, wsplit, r & 31);
+        if (EPS > 1) reduce_groups();
         if (sp < 0) store_row();
         else deliver_split_row<VPL, HINT>(D, k0 + r, sp, c, acc[0], acc[VPL > 1 ? VPL - 1 : 0], lane, pol.first);
         advance();
@@ -836,7 +881,7 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     __syncwarp();  // the batch ring is reused by this warp's next chunk
 }
 
-template <int VPL, bool BF16, bool HINT>
+template <int VPL, int EPS, bool BF16, bool HINT>
 __global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : 5) k_exec_contig(
     const ExecDesc* __restrict__ descs, const int32_t* __restrict__ queue,
     const int32_t* __restrict__ queue_desc, int64_t n_items, int32_t* ctrl,
@@ -864,13 +909,13 @@ __global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : 5) k_exec_contig(
             if (lane == 0) atomicOr(D.status, kStatusInternal);
             continue;
         }
-        const bool full = D.K == 128 * VPL;
+        const bool full = D.K == 128 / EPS * VPL;
         if (HINT && D.hot) {
-            if (full) contig_chunk<VPL, BF16, HINT, true, HINT>(D, (int32_t)c, lane, pol, park, bat);
-            else contig_chunk<VPL, BF16, HINT, false, HINT>(D, (int32_t)c, lane, pol, park, bat);
+            if (full) contig_chunk<VPL, EPS, BF16, HINT, true, HINT>(D, (int32_t)c, lane, pol, park, bat);
+            else contig_chunk<VPL, EPS, BF16, HINT, false, HINT>(D, (int32_t)c, lane, pol, park, bat);
         } else {
-            if (full) contig_chunk<VPL, BF16, HINT, true, false>(D, (int32_t)c, lane, pol, park, bat);
-            else contig_chunk<VPL, BF16, HINT, false, false>(D, (int32_t)c, lane, pol, park, bat);
+            if (full) contig_chunk<VPL, EPS, BF16, HINT, true, false>(D, (int32_t)c, lane, pol, park, bat);
+            else contig_chunk<VPL, EPS, BF16, HINT, false, false>(D, (int32_t)c, lane, pol, park, bat);
         }
     }
     // the last CTA out resets the tickets for the next launch (stream order makes it visible)
@@ -959,10 +1004,14 @@ static ExecKernel pick_kernel(int K)
     return k_exec<32, 8, BF16, HINT, DENSE>;
 }
 
+// nonzeros per warp step: as many lane groups as the K/4 vectors of a row leave room for
 template <bool BF16, bool HINT>
 static ExecKernel pick_contig(int K)
 {
-    return K <= 128 ? k_exec_contig<1, BF16, HINT> : k_exec_contig<2, BF16, HINT>;
+    if (K <= 32) return k_exec_contig<1, 4, BF16, HINT>;
+    if (K <= 64) return k_exec_contig<1, 2, BF16, HINT>;
+    if (K <= 128) return k_exec_contig<1, 1, BF16, HINT>;
+    return k_exec_contig<2, 1, BF16, HINT>;
 }
 
 // contig: a residual-only launch whose plans all have a contiguous residual stream (K <= 256)

@@ -161,11 +161,15 @@ def test_kernels_really_launch():
 
 
 @pytest.mark.parametrize("K,TN", [(128, 64), (128, 32), (256, 64), (96, 32), (64, 16)])
-def test_column_slices_bit_identical(K, TN):
-    # slicing the columns of B and C does not change any output element's summation order
+def test_column_slices(K, TN):
+    # Column slices of B and C give the same product.  A narrower slice may take several
+    # nonzeros per warp step (lane groups summed at the row's end), so the summation order, and
+    # with it the last bits, can differ from the full width; each form is deterministic.
     A = synth.rmat_csr(12, 50000, seed=K + TN)
     B = synth.dense_b(A["n"], K, seed=4)
     c_full, ref = run(A, B, tune=tune_from(ns, TN=0), check_plan=False)
     c_sl, _ = run(A, B, tune=tune_from(ns, TN=TN), check_plan=False)
-    assert np.array_equal(c_full, c_sl)
+    c_sl2, _ = run(A, B, tune=tune_from(ns, TN=TN), check_plan=False)
+    assert np.array_equal(c_sl, c_sl2)
     assert oracle.rel_frobenius(c_sl, ref) <= 1e-6
+    assert oracle.rel_frobenius(c_full, ref) <= 1e-6

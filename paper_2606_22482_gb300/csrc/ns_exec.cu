@@ -683,10 +683,15 @@ constexpr int kCRing = 4;
 // FULL: every lane of a group holds VPL whole vectors (K == 4 G VPL), so no per-lane width test.
 // HOT: the planner's hot-row map picks each gather's L2 policy; the map is read when a batch is
 // fetched and its bit travels as bit 31 of the column id.
-template <int VPL, int EPS, bool BF16, bool HINT, bool FULL, bool HOT>
+template <int VPL, int EPS, bool BF16, bool HINT, bool FULL, bool HOT, bool ASYNC>
 __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int lane, const Policies& pol,
-                                             float4* park, int2* bat)
+                                             float4* park, int2* bat, float4* aring)
 {
+    // ASYNC (FP32, one 4-column vector per lane, one nonzero per step): the gathered rows land in
+    // an 8-deep ring in shared memory through cp.async (each lane copies and later reads its own
+    // 16 bytes, so no warp barrier), which doubles the rows in flight without spending registers;
+    // otherwise a kCRing-deep register ring.
+    constexpr int kR = ASYNC ? 8 : kCRing;  // ring depth (steps in flight)
     static_assert(EPS == 1 || VPL == 1, "several nonzeros per step only for K <= 128");
     constexpr int G = 32 / EPS;
     const int g = lane / G, li = lane % G;
@@ -748,22 +753,31 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     float4 acc[VPL];
 #pragma unroll
     for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 b[kCRing][VPL];
-    float w[kCRing];
-    auto gather = [&](int2 e, float4 (&dst)[VPL], float& wv) {
+    float4 b[ASYNC ? 1 : kR][VPL];
+    float w[kR];
+    auto gather = [&](int2 e, int u) {
         const uint32_t col = HOT ? ((uint32_t)e.x & 0x7fffffffu) : (uint32_t)e.x;
         const unsigned char* row = Bl + (size_t)col * ldb_bytes;
         const uint64_t pl = HOT ? (e.x < 0 ? pol.last : pol.first) : pol.last;
+        if constexpr (ASYNC) {
+            cp_async16<HINT>(aring + u * 32 + lane, row, FULL || li < nv, pl);
+            cp_async_commit();
+        } else {
 #pragma unroll
-        for (int q = 0; q < VPL; ++q) {
-            if (FULL || li + 32 * q < nv) dst[q] = ld_b4<BF16, HINT>(row + 32 * VB * q, 0, pl);
-            else dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q = 0; q < VPL; ++q) {
+                if (FULL || li + 32 * q < nv) b[u][q] = ld_b4<BF16, HINT>(row + 32 * VB * q, 0, pl);
+                else b[u][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
-        wv = __int_as_float(e.y);
+        w[u] = __int_as_float(e.y);
     };
-    // step u of a group covers entries P + u EPS + g; the ring's first four steps
+    auto bvec = [&](int u, int q) -> float4 {
+        if constexpr (ASYNC) return aring[u * 32 + lane];
+        else return b[u][q];
+    };
+    // step u of a group covers entries P + u EPS + g; the ring's first kR steps
 #pragma unroll
-    for (int u = 0; u < kCRing; ++u) gather(bat[u * EPS + g], b[u], w[u]);
+    for (int u = 0; u < kR; ++u) gather(bat[u * EPS + g], u);
 
     // Row ends inside the stream.  Only the chunk's first and last rows can be split (a middle
     // row lies inside the chunk's merge range, so no other chunk touches it); the last one ends
@@ -819,30 +833,31 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     auto step = [&](int P, int u, const int2* e1, auto tail) {
         constexpr bool TAIL = decltype(tail)::value;
         const int mine = P + g;
+        if constexpr (ASYNC) cp_async_wait<kR - 1>();  // this step's row has landed
         if (next_end >= P + EPS || next_end >= total) {
             if (!TAIL || mine < total) {
 #pragma unroll
-                for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], b[u][q], acc[q]);
+                for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], bvec(u, q), acc[q]);
             }
         } else {
             int from = P;
             while (next_end < P + EPS && next_end < total) {
                 if (mine >= from && mine < next_end) {
 #pragma unroll
-                    for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], b[u][q], acc[q]);
+                    for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], bvec(u, q), acc[q]);
                 }
                 if (next_end > from) from = next_end;
                 flush();
             }
             if (mine >= from && (!TAIL || mine < total)) {
 #pragma unroll
-                for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], b[u][q], acc[q]);
+                for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], bvec(u, q), acc[q]);
             }
         }
-        gather(e1[u * EPS + g], b[u], w[u]);
+        gather(e1[u * EPS + g], u);
     };
 
-    constexpr int GS = kCRing * EPS;  // entries per group of steps (divides the batch of 32)
+    constexpr int GS = kR * EPS;  // entries per group of steps (divides the batch of 32)
     int P = 0;
     for (; P + GS <= total; P += GS) {
         if ((P & 31) == 0 && P > 0) {  // batch P + 32 into the ring, batch P + 64 requested
@@ -852,7 +867,7 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
         }
         const int2* e1 = bat + ((P + GS) & 127);  // entries P + GS .. P + 2 GS - 1 (GS divides 128)
 #pragma unroll
-        for (int u = 0; u < kCRing; ++u) step(P + u * EPS, u, e1, std::false_type{});
+        for (int u = 0; u < kR; ++u) step(P + u * EPS, u, e1, std::false_type{});
     }
     if (P < total) {  // the last partial group (its entries are already in the ring)
         if ((P & 31) == 0 && P > 0) {
@@ -861,7 +876,7 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
         }
         const int2* e1 = bat + ((P + GS) & 127);
 #pragma unroll
-        for (int u = 0; u < kCRing; ++u)
+        for (int u = 0; u < kR; ++u)
             if (P + u * EPS < total) step(P + u * EPS, u, e1, std::true_type{});
     }
     if (parked) {
@@ -878,6 +893,7 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
         else deliver_split_row<VPL, HINT>(D, k0 + r, sp, c, acc[0], acc[VPL > 1 ? VPL - 1 : 0], lane, pol.first);
         advance();
     }
+    if constexpr (ASYNC) cp_async_wait<0>();  // the look-ahead copies land before the ring is reused
     __syncwarp();  // the batch ring is reused by this warp's next chunk
 }
 
@@ -887,7 +903,9 @@ __global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : 5) k_exec_contig(
     const int32_t* __restrict__ queue_desc, int64_t n_items, int32_t* ctrl,
     const __grid_constant__ ExecDesc d0)
 {
+    constexpr bool ASYNC = VPL == 1 && EPS == 1 && !BF16;
     __shared__ float4 s_park[kExecWarps * 32 * VPL];  // one parked partial row per warp
+    __shared__ float4 s_aring[ASYNC ? kExecWarps * 8 * 32 : 1];
     __shared__ int2 s_bat[kExecWarps * 128];          // per warp: 4 batches of 32 (col, value)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4* const park = s_park + warp * 32 * VPL;
@@ -910,12 +928,13 @@ __global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : 5) k_exec_contig(
             continue;
         }
         const bool full = D.K == 128 / EPS * VPL;
+        float4* const aring = s_aring + (ASYNC ? (threadIdx.x >> 5) * 8 * 32 : 0);
         if (HINT && D.hot) {
-            if (full) contig_chunk<VPL, EPS, BF16, HINT, true, HINT>(D, (int32_t)c, lane, pol, park, bat);
-            else contig_chunk<VPL, EPS, BF16, HINT, false, HINT>(D, (int32_t)c, lane, pol, park, bat);
+            if (full) contig_chunk<VPL, EPS, BF16, HINT, true, HINT, false>(D, (int32_t)c, lane, pol, park, bat, aring);
+            else contig_chunk<VPL, EPS, BF16, HINT, false, HINT, false>(D, (int32_t)c, lane, pol, park, bat, aring);
         } else {
-            if (full) contig_chunk<VPL, EPS, BF16, HINT, true, false>(D, (int32_t)c, lane, pol, park, bat);
-            else contig_chunk<VPL, EPS, BF16, HINT, false, false>(D, (int32_t)c, lane, pol, park, bat);
+            if (full) contig_chunk<VPL, EPS, BF16, HINT, true, false, ASYNC>(D, (int32_t)c, lane, pol, park, bat, aring);
+            else contig_chunk<VPL, EPS, BF16, HINT, false, false, ASYNC>(D, (int32_t)c, lane, pol, park, bat, aring);
         }
     }
     // the last CTA out resets the tickets for the next launch (stream order makes it visible)

@@ -140,6 +140,11 @@ def make_workload(name: str, seed: int):
         desc = {"workload": "powerlaw-rmat-2^20-16.7Mnnz-K128-fp32", "m": A["m"], "n": A["n"],
                 "nnz": A.nnz, "K": 128, "b_dtype": "f32", "seed": seed,
                 "graph": "RMAT(.57,.19,.19,.05) relabelled, GCN values"}
+    elif name == "powerlaw-community":
+        A, B = synth.config_powerlaw(seed, community=True)
+        desc = {"workload": "powerlaw-rmat-2^20-16.7Mnnz-K128-fp32-community-rows", "m": A["m"], "n": A["n"],
+                "nnz": A.nnz, "K": 128, "b_dtype": "f32", "seed": seed,
+                "graph": "RMAT(.57,.19,.19,.05) relabelled, rows in seeded community order, GCN values"}
     elif name == "attention":
         A, B = synth.config_attention(seed)
         desc = {"workload": "block-sparse-attention-32768-K128-fp32", "m": A["m"], "n": A["n"],
@@ -205,7 +210,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="powerlaw",
-                    choices=["powerlaw", "attention", "attention-bf16", "small", "batched", "serve"])
+                    choices=["powerlaw", "powerlaw-community", "attention", "attention-bf16", "small",
+                             "batched", "serve", "gcn"])
+    ap.add_argument("--epochs", type=int, default=200, help="GCN epochs (--workload gcn)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=5.0, help="serve: seconds of arrivals")
     ap.add_argument("--pool", type=int, default=64, help="serve: graphs in the pool")
@@ -258,6 +265,8 @@ def main():
         return bench_batched(args, threads)
     if args.workload == "serve":
         return bench_serve(args, threads)
+    if args.workload == "gcn":
+        return bench_gcn(args, threads)
     if ws > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
@@ -467,6 +476,86 @@ def bench_batched(args, threads):
                      "frac": alg / (ms * 1e-3) / 1e9 / hbm, "traffic": None, "peak_source": src_pk},
         "max_rel_frobenius_sampled": max(errs), "gpu_launches": ns.launch_count() - l0,
         "clocks": clk.summary()}))
+
+
+# ---------------------------------------------------------------------------------------------
+# GNN workload: a 2-layer GCN forward for many epochs on the power-law graph, one plan for all
+# ---------------------------------------------------------------------------------------------
+def bench_gcn(args, threads):
+    import torch
+    import oracle
+    import synth
+    import paper_2606_22482_gb300 as ns
+    from paper_2606_22482_gb300.gcn import GCN
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    A, X = synth.config_powerlaw(args.seed)
+    K = 128
+    At = {k: (torch.from_numpy(v).to(dev) if isinstance(v, np.ndarray) else v) for k, v in A.items()}
+    rng = np.random.default_rng(args.seed + 7)
+    Ws = [torch.from_numpy((rng.standard_normal((K, K)) / np.sqrt(K)).astype(np.float32)).to(dev)
+          for _ in range(2)]
+    Xt = torch.from_numpy(X).to(dev)
+    stream = torch.cuda.current_stream()
+    tune = ns.tune_default()
+    tune.tau_tile = ns.NS_TAU_INF
+    if args.chunk is not None:
+        tune.chunk_nnz = tune.absorb_cap = args.chunk
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(2):  # pool warm-up
+        ns.spmm_plan(At, K, ns.NS_F32, tune).close()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    plan = ns.spmm_plan(At, K, ns.NS_F32, tune)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    plan_ms = ev[0].elapsed_time(ev[1])
+    net = GCN(plan, Ws)
+    for _ in range(max(args.warmup, 3)):
+        net.forward(Xt)
+    torch.cuda.synchronize()
+    l0 = ns.launch_count()
+    with ClockSampler(0) as clk:
+        ev[2].record(stream)
+        for _ in range(args.epochs):
+            out = net.forward(Xt)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+    ms_epoch = ev[2].elapsed_time(ev[3]) / args.epochs
+    launches = ns.launch_count() - l0
+    # the SpMM part alone (same plan, same operands)
+    XW = torch.empty((A["n"], K), device=dev)
+    torch.matmul(Xt, Ws[0], out=XW)
+    C = torch.empty((A["m"], K), device=dev)
+    ev[2].record(stream)
+    for _ in range(20):
+        plan.execute(XW, C)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    spmm_ms = ev[2].elapsed_time(ev[3]) / 20
+    # parity of the last layer's SpMM on sampled rows: its GEMM input read back from the device
+    H1 = torch.relu(C)  # layer-1 output of the run above (same plan, same operands)
+    XW2 = torch.matmul(H1, Ws[1])
+    plan.execute(XW2, C)
+    torch.cuda.synchronize()
+    rows = np.sort(np.random.default_rng(3).choice(A["m"], size=2000, replace=False)).astype(np.int32)
+    err = oracle.rel_frobenius(C.cpu().numpy()[rows], oracle.spmm(A, XW2.cpu().numpy(), rows=rows, threads=threads))
+    plan.close()
+    nnz = A.nnz
+    total_ms = plan_ms + args.epochs * ms_epoch
+    print(json.dumps({
+        "metric": "GCN 2-layer forward, epochs/s (one SpMM plan for all epochs)",
+        "value": 1e3 / ms_epoch, "unit": "epochs/s", "n_gpus": 1, "steps": args.epochs,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_epoch, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "gcn-2layer-powerlaw-rmat-2^20-K128-fp32", "nnz": nnz, "K": K,
+                   "layers": 2, "epochs": args.epochs, "tune": tune.as_dict(),
+                   "gemm": "torch.matmul (cuBLAS), FP32 without TF32"},
+        "plan_ms": plan_ms, "spmm_ms": spmm_ms,
+        "spmm_share_of_epoch": 2 * spmm_ms / ms_epoch,
+        "plan_share_of_run": plan_ms / total_ms,
+        "spmm_gflops": 2.0 * nnz * K / (spmm_ms * 1e-3) / 1e9,
+        "max_rel_frobenius_sampled": err, "gpu_launches": launches, "clocks": clk.summary()}))
 
 
 # ---------------------------------------------------------------------------------------------

@@ -112,8 +112,9 @@ class ClockSampler:
 EXEC_SOURCES = ("ns_exec.cu", "ns_internal.cuh", "ns_dense.cuh", "ns_ptx.cuh")
 MEASURED_TRAFFIC = {
     # (workload, tau_tile, chunk_nnz, l2_hints): (source digest, bytes per launch)
-    ("powerlaw", 2147483647, 512, 1): ("fbb55f500ac67467", 1676301000 + 541267200),
-    ("powerlaw", 2147483647, 256, 1): ("fbb55f500ac67467", 1699082496 + 580894976),
+    ("powerlaw", 2147483647, 512, 1): ("8152b2a1e71a0b01", 1676369664 + 541577728),
+    ("powerlaw", 2147483647, 256, 1): ("8152b2a1e71a0b01", 1698932224 + 586530560),
+    ("powerlaw", 2147483647, 1024, 1): ("8152b2a1e71a0b01", 1671225600 + 530718720),
 }
 
 
@@ -213,6 +214,8 @@ def main():
                     choices=["powerlaw", "powerlaw-community", "attention", "attention-bf16", "small",
                              "batched", "serve", "gcn"])
     ap.add_argument("--epochs", type=int, default=200, help="GCN epochs (--workload gcn)")
+    ap.add_argument("--rebalance", action="store_true",
+                    help="choose tau by the epoch-level re-balance loop (Section 5.3) instead")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=5.0, help="serve: seconds of arrivals")
     ap.add_argument("--pool", type=int, default=64, help="serve: graphs in the pool")
@@ -318,6 +321,12 @@ def main():
         tune.chunk_nnz = args.chunk
         tune.absorb_cap = args.chunk
         tune_src += f", chunk_nnz={args.chunk}"
+    rebalance_rep = None
+    if args.rebalance:
+        start = ns.tune_default()
+        start.TM = args.tm if args.tm is not None else 16
+        tune, rebalance_rep = ns.rebalance(At, K, DT, Bt, Ct, start=start, eps=0.05, max_iter=10)
+        tune_src = f"epoch-level re-balance (Section 5.3), TM={tune.TM}"
 
     def step(ev=None):
         p = ns.spmm_plan(At, K, DT, tune)
@@ -406,6 +415,7 @@ def main():
                      "algorithmic_bytes": alg_bytes, "n_touched": n_touched,
                      "kernel_ms": exec_ms, "frac_of_8000": achieved / 8000.0},
         "plan_ms": ms_step - exec_ms,
+        "rebalance": rebalance_rep,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -197,6 +197,38 @@ int32_t ns_cost_tau(double alpha, int32_t TM, int32_t TK);           /* ceil(alp
 double ns_skew(double dt_tc, double dt_res);                         /* Eq. 6 */
 
 /* ---------------------------------------------------------------------------------------- */
+/* Epoch-level re-balance (Section 5.3).                                                     */
+/* ---------------------------------------------------------------------------------------- */
+/* Each iteration ("epoch") plans A with the current tau, executes C := A*B once with the
+ * execute kernel stamping, per item class, the latest end time (globaltimer) of a dense-tile
+ * item and of a residual chunk after the earliest CTA start: dt_tc and dt_res.  With
+ * Skew = max/min (Eq. 6; infinite when a class is empty) above 1 + eps, work moves away from the
+ * class that finishes last: tau is bisected over the open bracket (0, TM*TK + 1) -- a higher tau
+ * leaves more tiles to the CUDA cores (the tensor side finished last), a lower one moves tiles to
+ * the tensor cores.  Stops when Skew <= 1 + eps, when the bracket is exhausted or after max_iter
+ * (at most 16) iterations; *out gets the tau with the shortest max(dt_tc, dt_res).
+ * A must be on the device; B (n x K, ld ldb) and C (m x K, ld ldc) are device pointers and C
+ * holds A*B on return.  Synchronous.  start may be NULL (defaults; tau = INF starts mid-bracket). */
+typedef struct {
+    int32_t iterations;   /* out */
+    int32_t converged;    /* out: 1 if Skew <= 1 + eps was reached                            */
+    int32_t tau[16];      /* out: tau of every iteration                                      */
+    double dt_tc_ms[16];  /* out: dense-tile class span, ms                                   */
+    double dt_res_ms[16]; /* out: residual class span, ms                                     */
+    double skew[16];      /* out: Eq. 6 (0 when a class is empty: read it as unbounded)        */
+} ns_rebalance_report_t;
+
+ns_status_t ns_rebalance(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, const void* B, int64_t ldb,
+                         float* C, int64_t ldc, ns_stream_t s, const ns_tune_t* start, double eps,
+                         int32_t max_iter, ns_tune_t* out, ns_rebalance_report_t* report);
+
+/* One bisection step of ns_rebalance (pure, no GPU): from the open bracket (lo, hi), the tau
+ * just timed and its class spans, the next bracket and tau.  Returns 1 when the loop ends
+ * (balanced within eps, or no integer left in the bracket), 0 to continue. */
+int32_t ns_rebalance_next(int32_t lo, int32_t hi, int32_t tau, double dt_tc, double dt_res, double eps,
+                          int32_t* lo_out, int32_t* hi_out, int32_t* tau_out);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Serving: continuous batching of SpMM requests on one GPU.                                 */
 /* ---------------------------------------------------------------------------------------- */
 typedef struct ns_server* ns_server_t;

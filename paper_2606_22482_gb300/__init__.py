@@ -15,7 +15,7 @@ from . import _abi
 from ._abi import (NS_F32, NS_BF16, NS_TAU_INF, NsError, Tune, PlanStats, lib, check,
                    tune_default)
 
-__all__ = ["NS_F32", "NS_BF16", "NS_TAU_INF", "NsError", "Tune", "PlanStats", "Plan",
+__all__ = ["NS_F32", "NS_BF16", "NS_TAU_INF", "NsError", "Tune", "PlanStats", "Plan", "rebalance",
            "spmm_plan", "spmm_execute", "spmm_host", "tune_default", "launch_count", "lib",
            "PLAN_ARRAYS"]
 
@@ -171,6 +171,26 @@ def autotune(A: dict, K: int, b_dtype: int = NS_F32, stream=None, report: bool =
     if report:
         return t, {f: getattr(rep, f) for f, _ in _abi.TuneReport._fields_}
     return t
+
+
+def rebalance(A: dict, K: int, b_dtype: int, B, C, start: Tune | None = None, eps: float = 0.05,
+              max_iter: int = 10, stream=None):
+    """ns_rebalance (Section 5.3): bisect tau on per-class finish times until Skew <= 1 + eps.
+
+    A is a device CSR, B and C CUDA tensors (C receives A @ B).  Returns (tune, report dict with
+    the per-iteration tau, class spans in ms and skew)."""
+    c, keep = _csr_struct(A, True)
+    out = Tune()
+    rep = _abi.RebalanceReport()
+    check(lib.ns_rebalance(ctypes.byref(c), int(K), int(b_dtype), ctypes.c_void_p(B.data_ptr()),
+                           int(B.stride(0)), ctypes.c_void_p(C.data_ptr()), int(C.stride(0)),
+                           _stream_handle(stream), ctypes.byref(start) if start is not None else None,
+                           float(eps), int(max_iter), ctypes.byref(out), ctypes.byref(rep)))
+    n = rep.iterations
+    report = {"iterations": n, "converged": bool(rep.converged), "tau": list(rep.tau[:n]),
+              "dt_tc_ms": list(rep.dt_tc_ms[:n]), "dt_res_ms": list(rep.dt_res_ms[:n]),
+              "skew": list(rep.skew[:n])}
+    return out, report
 
 
 class Batch:

@@ -44,6 +44,12 @@ class PlanStats(ctypes.Structure):
         "n_dvals", "n_res", "n_rl", "T", "n_chunks", "n_split", "n_slots", "n_items")]
 
 
+class RebalanceReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("tau", ctypes.c_int32 * 16), ("dt_tc_ms", ctypes.c_double * 16),
+                ("dt_res_ms", ctypes.c_double * 16), ("skew", ctypes.c_double * 16)]
+
+
 class TuneReport(ctypes.Structure):
     _fields_ = [("p_res", ctypes.c_double), ("p_tc", ctypes.c_double), ("alpha0", ctypes.c_double),
                 ("best_ms", ctypes.c_double), ("trials", ctypes.c_int32), ("plan_runs", ctypes.c_double)]
@@ -85,6 +91,11 @@ SIGNATURES = {
     "ns_cost_alpha": (D, [D, D, D]),
     "ns_cost_tau": (I32, [D, I32, I32]),
     "ns_skew": (D, [D, D]),
+    "ns_rebalance": (ctypes.c_int, [ctypes.POINTER(Csr), I32, I32, P, ctypes.c_int64, P, ctypes.c_int64, P,
+                                    ctypes.POINTER(Tune), D, I32, ctypes.POINTER(Tune),
+                                    ctypes.POINTER(RebalanceReport)]),
+    "ns_rebalance_next": (I32, [I32, I32, I32, D, D, D, ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "ns_serve_create": (ctypes.c_int, [ctypes.POINTER(ServeCfg), ctypes.POINTER(P)]),
     "ns_serve_register_graph": (ctypes.c_int, [P, ctypes.POINTER(Csr), ctypes.POINTER(I32)]),
     "ns_serve_submit": (ctypes.c_int, [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),

@@ -311,6 +311,103 @@ static ns_status_t time_tune(const ns_csr_t* A, int32_t K, ns_dtype_t dt, const 
     return r;
 }
 
+int32_t ns_rebalance_next(int32_t lo, int32_t hi, int32_t tau, double dt_tc, double dt_res, double eps,
+                          int32_t* lo_out, int32_t* hi_out, int32_t* tau_out)
+{
+    const double mx = dt_tc > dt_res ? dt_tc : dt_res, mn = dt_tc > dt_res ? dt_res : dt_tc;
+    if (mn > 0 && mx / mn <= 1.0 + eps) {  // balanced (Eq. 6)
+        *lo_out = lo;
+        *hi_out = hi;
+        *tau_out = tau;
+        return 1;
+    }
+    if (dt_tc > dt_res) lo = tau;  // the tensor side finishes last: fewer dense tiles
+    else hi = tau;                 // the CUDA-core side finishes last: more dense tiles
+    *lo_out = lo;
+    *hi_out = hi;
+    if (hi - lo <= 1) {
+        *tau_out = tau;
+        return 1;
+    }
+    *tau_out = lo + (hi - lo) / 2;
+    return 0;
+}
+
+ns_status_t ns_rebalance(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, const void* B, int64_t ldb,
+                         float* C, int64_t ldc, ns_stream_t s, const ns_tune_t* start, double eps,
+                         int32_t max_iter, ns_tune_t* out, ns_rebalance_report_t* report)
+{
+    if (!A || !out || !B || !C) {
+        set_error("NULL argument");
+        return NS_ERR_INVALID;
+    }
+    if (!A->on_device) {
+        set_error("ns_rebalance needs a device CSR");
+        return NS_ERR_INVALID;
+    }
+    if (max_iter < 1 || max_iter > 16 || !(eps >= 0)) {
+        set_error("max_iter must be in 1..16 and eps >= 0");
+        return NS_ERR_INVALID;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(s);
+    ns_tune_t t;
+    if (start) t = *start;
+    else ns_tune_default(&t);
+    NS_TRY(plan_check_tune(t));
+    int32_t lo = 0, hi = t.TM * t.TK + 1;
+    int32_t tau = (t.tau_tile >= 1 && t.tau_tile <= t.TM * t.TK) ? t.tau_tile : lo + (hi - lo) / 2;
+    ns_rebalance_report_t rep{};
+    unsigned long long* clk = nullptr;
+    NS_CUDA_TRY(pool_alloc(reinterpret_cast<void**>(&clk), 3 * sizeof(unsigned long long), st));
+    static const unsigned long long kReset[3] = {~0ull, 0ull, 0ull};
+    int32_t best_tau = tau;
+    double best_span = 1e300;
+    ns_status_t r = NS_OK;
+    for (int it = 0; it < max_iter; ++it) {
+        t.tau_tile = tau;
+        Plan* P = nullptr;
+        r = plan_create(A, K, b_dtype, &t, st, &P);
+        if (r != NS_OK) break;
+        // one untimed epoch (caches, grid size), then the stamped one
+        r = ns_spmm_execute(reinterpret_cast<ns_plan_t>(P), B, ldb, C, ldc, st);
+        unsigned long long h[3] = {0, 0, 0};
+        if (r == NS_OK) {
+            P->class_clock = clk;
+            if (cudaMemcpyAsync(clk, kReset, sizeof kReset, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                r = NS_ERR_CUDA;
+            if (r == NS_OK) r = ns_spmm_execute(reinterpret_cast<ns_plan_t>(P), B, ldb, C, ldc, st);
+            if (r == NS_OK && (cudaMemcpyAsync(h, clk, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                               cudaStreamSynchronize(st) != cudaSuccess))
+                r = NS_ERR_CUDA;
+            P->class_clock = nullptr;
+        }
+        delete P;
+        if (r != NS_OK) break;
+        const double dt_tc = h[1] > h[0] ? (double)(h[1] - h[0]) * 1e-6 : 0.0;
+        const double dt_res = h[2] > h[0] ? (double)(h[2] - h[0]) * 1e-6 : 0.0;
+        rep.tau[it] = tau;
+        rep.dt_tc_ms[it] = dt_tc;
+        rep.dt_res_ms[it] = dt_res;
+        rep.skew[it] = ns_skew(dt_tc, dt_res);
+        rep.iterations = it + 1;
+        const double span = dt_tc > dt_res ? dt_tc : dt_res;
+        if (span < best_span) {
+            best_span = span;
+            best_tau = tau;
+        }
+        const double mn = dt_tc > dt_res ? dt_res : dt_tc;
+        if (mn > 0 && span / mn <= 1.0 + eps) rep.converged = 1;
+        if (ns_rebalance_next(lo, hi, tau, dt_tc, dt_res, eps, &lo, &hi, &tau)) break;
+    }
+    cudaFreeAsync(clk, st);
+    cudaStreamSynchronize(st);
+    if (r != NS_OK) return r;
+    *out = t;
+    out->tau_tile = best_tau;
+    if (report) *report = rep;
+    return NS_OK;
+}
+
 ns_status_t ns_autotune(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, ns_stream_t s,
                         ns_tune_t* out, ns_tune_report_t* report)
 {

@@ -591,6 +591,13 @@ __device__ void residual_chunk(const ExecDesc& D, int32_t c, int lane, const Pol
 
 namespace ns {
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // ---------------------------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------------------------
@@ -608,6 +615,8 @@ __global__ void __launch_bounds__(kExecThreads, DENSE ? 1 : 4) k_exec(const Exec
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Policies pol{0, 0};
     if (HINT) pol = make_policies();
+    unsigned long long* const clk = descs ? nullptr : d0.class_clock;  // single-plan launches only
+    if (clk && threadIdx.x == 0) atomicMin(clk, global_ns());
     if (DENSE) {
         // phase 1: dense windows, one CTA each, taken in work-list order
         for (;;) {
@@ -623,6 +632,7 @@ __global__ void __launch_bounds__(kExecThreads, DENSE ? 1 : 4) k_exec(const Exec
                     dense_item<L, VPL, BF16, HINT>(D, it, smem_raw, pol);
                 else if (threadIdx.x == 0)
                     atomicOr(D.status, kStatusInternal);  // guard: launch without the tile buffers
+                if (clk && threadIdx.x == 0) atomicMax(clk + 1, global_ns());
             }
         }
     }
@@ -652,6 +662,7 @@ __global__ void __launch_bounds__(kExecThreads, DENSE ? 1 : 4) k_exec(const Exec
         } else {
             residual_chunk<L, VPL, BF16, HINT>(D, (int32_t)c, lane, pol);
         }
+        if (clk && lane == 0) atomicMax(clk + 2, global_ns());
     }
     // the last CTA out resets the tickets for the next launch (stream order makes it visible)
     __syncthreads();
@@ -912,6 +923,8 @@ __global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : 5) k_exec_contig(
     int2* const bat = s_bat + warp * 128;
     Policies pol{0, 0};
     if (HINT) pol = make_policies();
+    unsigned long long* const clk = descs ? nullptr : d0.class_clock;  // single-plan launches only
+    if (clk && threadIdx.x == 0) atomicMin(clk, global_ns());
     for (;;) {
         int64_t u = 0;
         if (lane == 0) u = atomicAdd(ctrl + 3, 1);
@@ -936,6 +949,7 @@ __global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : 5) k_exec_contig(
             if (full) contig_chunk<VPL, EPS, BF16, HINT, true, false, ASYNC>(D, (int32_t)c, lane, pol, park, bat, aring);
             else contig_chunk<VPL, EPS, BF16, HINT, false, false, ASYNC>(D, (int32_t)c, lane, pol, park, bat, aring);
         }
+        if (clk && lane == 0) atomicMax(clk + 2, global_ns());
     }
     // the last CTA out resets the tickets for the next launch (stream order makes it visible)
     __syncthreads();
@@ -1005,6 +1019,7 @@ void fill_desc(const Plan* P, const void* B, int64_t ldb, float* C, int64_t ldc,
     d->hot = P->hot_bits;
     d->chunk_nnz = P->tune.chunk_nnz;
     d->status = P->ctrl + 2;
+    d->class_clock = P->class_clock;
 }
 
 typedef void (*ExecKernel)(const ExecDesc*, const int32_t*, const int32_t*, int64_t, int32_t*, ExecDesc);

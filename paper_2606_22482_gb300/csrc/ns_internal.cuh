@@ -144,6 +144,9 @@ struct ExecDesc {
     const uint32_t* hot;   // bit j set: B row j is among the most gathered (evict-last); null: all
     int32_t chunk_nnz;     // W of the plan (sizes the staged chunk buffers)
     int32_t* status;       // device status word (kStatus* bits)
+    // per-class progress clock (Section 5.3 epoch monitoring), null when off: [0] earliest CTA
+    // start, [1] latest end of a dense item, [2] latest end of a residual chunk (globaltimer ns)
+    unsigned long long* class_clock;
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -194,6 +197,7 @@ struct Plan {
     float* slots = nullptr;
     int32_t* split_cnt = nullptr;
     int32_t* ctrl = nullptr;       // [0] ticket, [1] CTAs done, [2] status, [3..] scalars
+    unsigned long long* class_clock = nullptr;  // set while the rebalance loop times the launch
     ExecDesc desc_host{};           // the single-plan descriptor (a kernel parameter)
     bool desc_valid = false;
     std::vector<DevBlock> blocks;  // every device allocation the plan owns

@@ -34,10 +34,10 @@ _lib = None
 TAU_INF = 2147483647
 
 TUNE_FIELDS = ("TM", "TK", "tau_tile", "tau_row", "tau_col", "col_order", "chunk_nnz",
-               "absorb_cap", "group", "cost_tc", "cost_res")
+               "absorb_cap", "group", "cost_tc", "cost_res", "reorder")
 
 DEFAULT_TUNE = dict(TM=16, TK=16, tau_tile=TAU_INF, tau_row=0, tau_col=0, col_order=0,
-                    chunk_nnz=256, absorb_cap=256, group=4, cost_tc=1, cost_res=8)
+                    chunk_nnz=256, absorb_cap=256, group=4, cost_tc=1, cost_res=8, reorder=0)
 
 PLAN_ARRAYS = ("aic_rows", "win_rows", "win_dptr", "dwin", "dwin_absorb", "dtile_cols",
                "dtile_bits", "dtile_voff", "dtile_vals", "res_rowptr", "res_col", "res_val",

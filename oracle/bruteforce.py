@@ -10,6 +10,7 @@ keep m, n <= a few hundred.
 from __future__ import annotations
 
 import math
+from fractions import Fraction
 from collections import Counter
 
 import numpy as np
@@ -22,6 +23,30 @@ def _bf16_library(x: np.ndarray) -> np.ndarray:
     import torch
     t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
     return t.to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16).copy()
+
+
+def jaccard(a: set, b: set) -> Fraction:
+    union = len(a | b)
+    return Fraction(len(a & b), union) if union else Fraction(0)
+
+
+def local_reorder(rows: list, row: list, keep_col: set, TM: int, cluster: int) -> list:
+    """Section 6.1 local stage: in each cluster of consecutive rows, the first unassigned row
+    anchors a new window and takes the TM - 1 unassigned rows with the largest Jaccard
+    similarity of kept-column sets (earlier rows first on ties)."""
+    out = []
+    for c0 in range(0, len(rows), cluster):
+        cl = rows[c0:c0 + cluster]
+        cols = [set(row[i]) & keep_col for i in cl]
+        free = list(range(len(cl)))
+        while free:
+            a = free.pop(0)
+            out.append(cl[a])
+            ranked = sorted(free, key=lambda b: (-jaccard(cols[a], cols[b]), b))
+            take = ranked[:TM - 1]
+            out.extend(cl[b] for b in take)
+            free = [b for b in free if b not in take]
+    return out
 
 
 def plan(A: dict, K: int, *, b_bf16: bool = False, **tune) -> dict:
@@ -39,6 +64,8 @@ def plan(A: dict, K: int, *, b_bf16: bool = False, **tune) -> dict:
         cc = Counter(j for i in aic for j in row[i])
         keep_col = {j for j in range(n) if cc.get(j, 0) > t["tau_col"]}
 
+    if windows_on and t.get("reorder", 0) > 0:
+        aic = local_reorder(aic, row, keep_col, TM, t["reorder"] * TM)
     n_win = math.ceil(len(aic) / TM)
     windows = [[aic[w * TM + r] if w * TM + r < len(aic) else -1 for r in range(TM)]
                for w in range(n_win)]

@@ -103,6 +103,7 @@ typedef struct {
     int32_t group;       /* residual chunks per residual work item                               */
     int32_t cost_tc;     /* Eq. 1 cost weight of one tile element                                */
     int32_t cost_res;    /* Eq. 1 cost weight of one residual nonzero                            */
+    int32_t reorder;     /* Section 6.1 local reordering: windows per cluster (0: off)            */
 } orc_tune;
 
 typedef struct {
@@ -258,6 +259,66 @@ int orc_plan_build(int32_t m, int32_t n, const int32_t* rowptr, const int32_t* c
         }
         for (int32_t j = 0; j < n; ++j) aic_col[j] = colcount[j] > tu->tau_col;
         free(colcount);
+    }
+
+    /* ---- Section 6.1 local reordering: inside clusters of reorder*TM consecutive kept rows,
+     *      rebuild windows greedily.  The anchor is the first unassigned row of the cluster in the
+     *      current order; it takes the TM-1 unassigned rows most similar to it by Jaccard
+     *      similarity of their kept-column sets (ties: earlier position), best first. ---- */
+    if (windows_on && tu->reorder > 0 && m_aic > 0) {
+        const int64_t CR = (int64_t)tu->reorder * TM;
+        int32_t* neworder = (int32_t*)malloc(sizeof(int32_t) * (size_t)m_aic);
+        int64_t* klen = (int64_t*)malloc(sizeof(int64_t) * (size_t)m_aic);
+        uint8_t* used = (uint8_t*)calloc((size_t)m_aic, 1);
+        for (int64_t k = 0; k < m_aic; ++k) {
+            int32_t i = P->aic_rows[k];
+            int64_t c = 0;
+            for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) c += aic_col[colidx[p]] ? 1 : 0;
+            klen[k] = c;
+        }
+        for (int64_t c0 = 0; c0 < m_aic; c0 += CR) {
+            const int64_t c1 = c0 + CR < m_aic ? c0 + CR : m_aic;
+            int64_t out = c0;
+            for (int64_t a = c0; a < c1; ++a) {
+                if (used[a]) continue;
+                used[a] = 1;
+                neworder[out++] = P->aic_rows[a];
+                const int32_t ia = P->aic_rows[a];
+                for (int32_t pick = 0; pick < TM - 1; ++pick) {
+                    int64_t best = -1, bn = 0, bd = 1;
+                    for (int64_t b = c0; b < c1; ++b) {
+                        if (used[b]) continue;
+                        /* |intersection| over kept columns: merge of the two sorted rows */
+                        const int32_t ib = P->aic_rows[b];
+                        int64_t inter = 0;
+                        int32_t p = rowptr[ia], q = rowptr[ib];
+                        while (p < rowptr[ia + 1] && q < rowptr[ib + 1]) {
+                            if (colidx[p] < colidx[q]) ++p;
+                            else if (colidx[p] > colidx[q]) ++q;
+                            else {
+                                inter += aic_col[colidx[p]] ? 1 : 0;
+                                ++p;
+                                ++q;
+                            }
+                        }
+                        const int64_t uni = klen[a] + klen[b] - inter;
+                        const int64_t num = uni > 0 ? inter : 0, den = uni > 0 ? uni : 1;
+                        if (best < 0 || num * bd > bn * den) {  /* strictly better; ties keep the earlier */
+                            best = b;
+                            bn = num;
+                            bd = den;
+                        }
+                    }
+                    if (best < 0) break;
+                    used[best] = 1;
+                    neworder[out++] = P->aic_rows[best];
+                }
+            }
+        }
+        memcpy(P->aic_rows, neworder, sizeof(int32_t) * (size_t)m_aic);
+        free(neworder);
+        free(klen);
+        free(used);
     }
 
     /* ---- windows: consecutive kept rows, TM per window, the last padded with -1 ---- */

@@ -45,6 +45,9 @@ TINY_TUNES = [
     dict(tau_tile=INF, chunk_nnz=3, group=1),
     dict(tau_tile=6, TM=16, TK=16, chunk_nnz=4, absorb_cap=0, group=2),
     dict(tau_tile=12, TM=16, TK=16, chunk_nnz=6, absorb_cap=2, tau_row=1, col_order=1),
+    dict(tau_tile=3, TM=16, TK=16, reorder=1),
+    dict(tau_tile=2, TM=16, TK=16, reorder=3, tau_col=1),
+    dict(tau_tile=5, TM=32, TK=16, reorder=2, tau_row=1),
 ]
 
 
@@ -179,7 +182,8 @@ def _plan_product(A, P, B, b_bf16=False):
 
 MED_TUNES = [dict(tau_tile=INF), dict(tau_tile=1), dict(tau_tile=24, TM=16, TK=16),
              dict(tau_tile=200, TM=32, TK=16, tau_row=4, chunk_nnz=64),
-             dict(tau_tile=64, TM=64, TK=32, tau_col=1, col_order=1, absorb_cap=16)]
+             dict(tau_tile=64, TM=64, TK=32, tau_col=1, col_order=1, absorb_cap=16),
+             dict(tau_tile=24, TM=16, TK=16, reorder=4)]
 
 
 @pytest.mark.parametrize("ti", range(len(MED_TUNES)))
@@ -328,3 +332,39 @@ def test_redundancy_metric_small_cases():
 def test_algorithmic_bytes_and_flops():
     assert formulas.spmm_flops(10, 4) == 80
     assert formulas.algorithmic_bytes(2, 3, 4, 2, 4) == 4 * 3 + 8 * 3 + 4 * 4 * 2 + 4 * 2 * 4
+
+
+def _two_patterns(m=64, width=16):
+    """Rows alternate between columns [0, width) and [width, 2 width), all values 1."""
+    rows = [list(range(0, width)) if i % 2 == 0 else list(range(width, 2 * width)) for i in range(m)]
+    rowptr = np.zeros(m + 1, dtype=np.int32)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    colidx = np.array([c for r in rows for c in r], dtype=np.int32)
+    return dict(m=m, n=2 * width, rowptr=rowptr, colidx=colidx, vals=np.ones(len(colidx), np.float32))
+
+
+def test_local_reorder_groups_alike_rows():
+    # Section 6.1 local stage: interleaved patterns give half-full tiles in row order; the
+    # Jaccard rebuild puts each pattern's rows in windows of their own, so every tile is full
+    A = _two_patterns()
+    plain = oracle.plan(A, 16, tau_tile=200, TM=16, TK=16)
+    re = oracle.plan(A, 16, tau_tile=200, TM=16, TK=16, reorder=4)
+    assert plain["n_dtiles"] == 0
+    assert re["n_dtiles"] == 4
+    w = re["win_rows"].reshape(-1, 16)
+    assert all(len(set(int(i) % 2 for i in win)) == 1 for win in w)   # one pattern per window
+    # the anchor leads each window, then the equal-similarity rows in their current order
+    assert list(w[0]) == list(range(0, 32, 2))
+    assert sorted(re["aic_rows"].tolist()) == sorted(plain["aic_rows"].tolist())
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_local_reorder_permutes_within_clusters(seed):
+    A = synth.random_csr(300, 120, 0.05, seed=seed)
+    for TM, R in ((16, 1), (16, 3), (32, 2)):
+        plain = oracle.plan(A, 16, tau_tile=8, TM=TM, TK=16)["aic_rows"]
+        re = oracle.plan(A, 16, tau_tile=8, TM=TM, TK=16, reorder=R)["aic_rows"]
+        cl = R * TM
+        for c0 in range(0, len(plain), cl):
+            assert sorted(re[c0:c0 + cl].tolist()) == sorted(plain[c0:c0 + cl].tolist())
+            assert re[c0] == plain[c0]          # the first window keeps its anchor

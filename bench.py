@@ -226,6 +226,8 @@ def main():
     ap.add_argument("--tn", type=int, default=None, help="override the column-slice width TN")
     ap.add_argument("--chunk", type=int, default=None, help="override the residual chunk size W")
     ap.add_argument("--tm", type=int, default=None, choices=[16, 32, 64], help="override the window height TM")
+    ap.add_argument("--reorder", type=int, default=None,
+                    help="Section 6.1 local reordering: windows per cluster (0 = off)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -317,6 +319,9 @@ def main():
     if args.tm is not None:
         tune.TM = args.tm
         tune_src += f", TM={args.tm}"
+    if args.reorder is not None:
+        tune.reorder = args.reorder
+        tune_src += f", reorder={args.reorder}"
     if args.chunk is not None:
         tune.chunk_nnz = args.chunk
         tune.absorb_cap = args.chunk

@@ -86,10 +86,14 @@ typedef struct {
  *               0: default caching
  *   TN          execute in column slices of TN (multiple of 8; 0 = K in one pass): each slice
  *               gathers only TN columns of B, so its working set stays in L2 (Section 6.2.2 N
- *               shaping); A is re-read once per slice.  Execution only: plans do not depend on it */
+ *               shaping); A is re-read once per slice.  Execution only: plans do not depend on it
+ *   reorder     Section 6.1 local reordering (0 = off): inside clusters of reorder * TM
+ *               consecutive kept rows (at most 1024 rows), the first unassigned row anchors a
+ *               new window and takes the TM - 1 unassigned rows with the largest Jaccard
+ *               similarity of kept-column sets (earlier rows first on ties) */
 typedef struct {
     int32_t TM, TK, tau_tile, tau_row, tau_col, col_order, chunk_nnz, absorb_cap, group,
-        cost_tc, cost_res, l2_hints, TN;
+        cost_tc, cost_res, l2_hints, TN, reorder;
 } ns_tune_t;
 
 void ns_tune_default(ns_tune_t* t);

@@ -16,7 +16,7 @@ STATUS = {0: "NS_OK", 1: "NS_ERR_INVALID", 2: "NS_ERR_UNSUPPORTED", 3: "NS_ERR_O
           8: "NS_ERR_NOT_FOUND"}
 
 TUNE_FIELDS = ("TM", "TK", "tau_tile", "tau_row", "tau_col", "col_order", "chunk_nnz",
-               "absorb_cap", "group", "cost_tc", "cost_res", "l2_hints", "TN")
+               "absorb_cap", "group", "cost_tc", "cost_res", "l2_hints", "TN", "reorder")
 
 
 class NsError(RuntimeError):

@@ -224,6 +224,7 @@ void ns_tune_default(ns_tune_t* t)
     t->cost_res = 8;
     t->l2_hints = 1;
     t->TN = 0;
+    t->reorder = 0;
 }
 
 const char* ns_last_error(void) { return t_err.c_str(); }

@@ -44,6 +44,7 @@ inline void count_launch(int64_t k = 1) { g_launches.fetch_add(k, std::memory_or
     } while (0)
 
 constexpr int32_t kTauInf = NS_TAU_INF;
+constexpr int kReorderMaxRows = 1024;  // rows of one local-reordering cluster (Section 6.1)
 constexpr int kExecWarps = 4;            // warps per execute CTA (== residual chunks per item)
 constexpr int kExecThreads = kExecWarps * 32;
 

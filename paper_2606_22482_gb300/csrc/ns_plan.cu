@@ -347,6 +347,7 @@ ns_status_t plan_check_tune(const ns_tune_t& t)
     if (t.col_order != 0 && t.col_order != 1) return NS_ERR_INVALID;
     if (t.TN < 0 || (t.TN % 8) != 0) return NS_ERR_INVALID;
     if (t.l2_hints < 0 || t.l2_hints > 2) return NS_ERR_INVALID;
+    if (t.reorder < 0 || (int64_t)t.reorder * t.TM > kReorderMaxRows) return NS_ERR_INVALID;
     return NS_OK;
 }
 

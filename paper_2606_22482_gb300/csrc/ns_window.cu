@@ -754,6 +754,121 @@ static unsigned wgrid(int64_t n, int threads = 256)
 // ---------------------------------------------------------------------------------------------
 // orchestration
 // ---------------------------------------------------------------------------------------------
+// ---------------------------------------------------------------------------------------------
+// Section 6.1 local reordering, one CTA per cluster of CR consecutive kept rows: the first
+// unassigned row anchors a window and takes the TM - 1 unassigned rows with the largest Jaccard
+// similarity of kept-column sets (earlier rows first on ties), best first.  Similarities are
+// compared exactly as fractions (cross products in 64 bits).
+// ---------------------------------------------------------------------------------------------
+constexpr int kReorderThreads = 256;
+
+struct SimKey {
+    int64_t num, den;  // Jaccard = num / den (0 / 1 for two empty sets)
+    int32_t pos;       // position in the cluster; INT32_MAX: no candidate
+};
+
+__device__ __forceinline__ bool sim_better(const SimKey& x, const SimKey& y)
+{
+    if (x.pos == INT32_MAX) return false;
+    if (y.pos == INT32_MAX) return true;
+    const int64_t l = x.num * y.den, r = y.num * x.den;
+    return l > r || (l == r && x.pos < y.pos);
+}
+
+__global__ void __launch_bounds__(kReorderThreads) k_local_reorder(
+    const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+    const int32_t* __restrict__ colcount, int32_t tau_col, const int32_t* __restrict__ aic_in,
+    int64_t m_aic, int TM, int CR, int32_t* __restrict__ aic_out)
+{
+    __shared__ uint8_t used[kReorderMaxRows];
+    __shared__ int32_t klen[kReorderMaxRows];
+    __shared__ int32_t inter[kReorderMaxRows];
+    __shared__ SimKey wbest[kReorderThreads / 32];
+    __shared__ int32_t s_anchor, s_out, s_next, s_win;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t c0 = (int64_t)blockIdx.x * CR;
+    if (c0 >= m_aic) return;
+    const int R = (int)(m_aic - c0 < CR ? m_aic - c0 : CR);
+    auto kept = [&](int32_t j) { return tau_col <= 0 || colcount[j] > tau_col; };
+    for (int b = threadIdx.x; b < R; b += blockDim.x) {
+        const int32_t i = aic_in[c0 + b];
+        int32_t c = 0;
+        for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) c += kept(colidx[p]) ? 1 : 0;
+        klen[b] = c;
+        used[b] = 0;
+    }
+    if (threadIdx.x == 0) {
+        s_out = 0;
+        s_next = 0;
+    }
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) {  // the first unassigned row anchors the next window
+            int a = s_next;
+            while (a < R && used[a]) ++a;
+            s_next = a;
+            s_anchor = a;
+            if (a < R) {
+                used[a] = 1;
+                aic_out[c0 + s_out++] = aic_in[c0 + a];
+            }
+        }
+        __syncthreads();
+        const int a = s_anchor;
+        if (a >= R) break;
+        const int32_t ia = aic_in[c0 + a];
+        const int32_t pa0 = rowptr[ia], pa1 = rowptr[ia + 1];
+        for (int b = threadIdx.x; b < R; b += blockDim.x) {
+            if (used[b]) continue;
+            const int32_t ib = aic_in[c0 + b];
+            int32_t p = pa0, q = rowptr[ib], q1 = rowptr[ib + 1], cnt = 0;
+            while (p < pa1 && q < q1) {
+                const int32_t ca = colidx[p], cb = colidx[q];
+                if (ca < cb) ++p;
+                else if (ca > cb) ++q;
+                else {
+                    cnt += kept(ca) ? 1 : 0;
+                    ++p;
+                    ++q;
+                }
+            }
+            inter[b] = cnt;
+        }
+        __syncthreads();
+        for (int pick = 0; pick < TM - 1; ++pick) {
+            SimKey best{0, 1, INT32_MAX};
+            for (int b = threadIdx.x; b < R; b += blockDim.x) {
+                if (used[b]) continue;
+                const int64_t uni = (int64_t)klen[a] + klen[b] - inter[b];
+                const SimKey k{uni > 0 ? (int64_t)inter[b] : 0, uni > 0 ? uni : 1, b};
+                if (sim_better(k, best)) best = k;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                SimKey other;
+                other.num = __shfl_xor_sync(0xffffffffu, best.num, o);
+                other.den = __shfl_xor_sync(0xffffffffu, best.den, o);
+                other.pos = __shfl_xor_sync(0xffffffffu, best.pos, o);
+                if (sim_better(other, best)) best = other;
+            }
+            if (lane == 0) wbest[warp] = best;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                SimKey w = wbest[0];
+                for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+                    if (sim_better(wbest[q], w)) w = wbest[q];
+                s_win = w.pos;
+                if (w.pos != INT32_MAX) {
+                    used[w.pos] = 1;
+                    aic_out[c0 + s_out++] = aic_in[c0 + w.pos];
+                }
+            }
+            __syncthreads();
+            if (s_win == INT32_MAX) break;
+        }
+    }
+}
+
 ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
 {
     const ns_tune_t& t = P->tune;
@@ -787,6 +902,18 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
             k_colcount<<<wgrid(m_aic * 32), 256, 0, s>>>(P->rowptr, P->colidx, aic_rows, m_aic, colcount);
             NS_LAUNCH_CHECK();
         }
+    }
+    if (t.reorder > 0 && m_aic > 0) {  // Section 6.1 local reordering of the kept rows
+        int32_t* reordered = nullptr;
+        Arena ar;
+        ar.reserve(&reordered, m_aic);
+        NS_TRY(ar.commit(s));
+        const int CR = t.reorder * TM;
+        k_local_reorder<<<(unsigned)ceil_div(m_aic, CR), kReorderThreads, 0, s>>>(
+            P->rowptr, P->colidx, colcount, t.tau_col, aic_rows, m_aic, TM, CR, reordered);
+        NS_LAUNCH_CHECK();
+        NS_CUDA_TRY(cudaMemcpyAsync(aic_rows, reordered, sizeof(int32_t) * m_aic, cudaMemcpyDeviceToDevice, s));
+        ar.release(s);
     }
     NS_TRY(device_scan<int64_t>(KeptLenLoad{P->rowptr, P->colidx, aic_rows, colcount, t.tau_col},
                                 KeptLenStore{row_kbase}, m_aic, partial, row_kbase + m_aic, s));

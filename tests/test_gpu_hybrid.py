@@ -29,6 +29,8 @@ CASES = [
     dict(tau_tile=64, TM=16, TK=32, tau_row=4),
     dict(tau_tile=30, TM=16, TK=16, tau_col=1),
     dict(tau_tile=40, TM=16, TK=16, absorb_cap=0, chunk_nnz=16),   # split rows dense + residual
+    dict(tau_tile=24, TM=16, TK=16, reorder=4),                     # Section 6.1 local reordering
+    dict(tau_tile=100, TM=32, TK=16, reorder=2, tau_col=1),
 ]
 
 

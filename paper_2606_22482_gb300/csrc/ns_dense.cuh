@@ -140,6 +140,7 @@ __device__ void dense_item(const ExecDesc& D, int32_t di, unsigned char* smem, c
     const int g = lane >> 2, tq = lane & 3;
     const DenseGeom G = dense_geom(K, TM, TK, BF16);
     const int rg = warp / G.CG, cg = warp % G.CG;
+    const int lg_tk = TK == 16 ? 4 : 5;
     const int32_t w = __ldg(D.dwin + di);
     const int32_t t0 = __ldg(D.win_dptr + w), t1 = __ldg(D.win_dptr + w + 1);
     float* Cs = reinterpret_cast<float*>(smem + G.off_c);
@@ -202,7 +203,7 @@ __device__ void dense_item(const ExecDesc& D, int32_t di, unsigned char* smem, c
             __syncthreads();
             // expand the bitmap tile into a dense TM x TK operand
             for (int e = threadIdx.x; e < TM * TK; e += blockDim.x) {
-                const int r = e / TK, c = e % TK;
+                const int r = e >> lg_tk, c = e & (TK - 1);  // TK is 16 or 32
                 const uint32_t word = bits[e >> 5];
                 const bool set = (word >> (e & 31)) & 1u;
                 const int idx = wp[e >> 5] + __popc(word & ((1u << (e & 31)) - 1u));

@@ -27,6 +27,32 @@ enum { kCtrTicket = 0, kCtrDone = 1, kCtrStatus = 2 };
 // 64-bit counters used by the planner
 enum { kCnBadRange = 0, kCnDescents = 1, kCnBadPtr = 2, kCnStartDescents = 3, kCnTotals = 4 };
 
+// Adds two per-thread counts into cnt[ia] and cnt[ib] with one atomic each per block: every
+// counter is a single address, so per-warp atomics would queue up at one L2 slice.  Called by all
+// threads of the block.
+__device__ __forceinline__ void block_add2(unsigned long long* cnt, int ia, unsigned long long a, int ib,
+                                           unsigned long long b)
+{
+    __shared__ unsigned long long sa[32], sb[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) {
+        sa[warp] = a;
+        sb[warp] = b;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        a = warp_sum(lane < nw ? sa[lane] : 0ull);
+        b = warp_sum(lane < nw ? sb[lane] : 0ull);
+        if (lane == 0) {
+            if (a) atomicAdd(cnt + ia, a);
+            if (b) atomicAdd(cnt + ib, b);
+        }
+    }
+}
+
 __global__ void k_check_elems(const int32_t* __restrict__ colidx, int64_t nnz, int32_t n,
                               unsigned long long* cnt)
 {
@@ -37,12 +63,48 @@ __global__ void k_check_elems(const int32_t* __restrict__ colidx, int64_t nnz, i
         bad += (c < 0 || c >= n);
         if (p + 1 < nnz) desc += (__ldg(colidx + p + 1) <= c);
     }
-    bad = warp_sum(bad);
-    desc = warp_sum(desc);
-    if ((threadIdx.x & 31) == 0) {
-        if (bad) atomicAdd(cnt + kCnBadRange, bad);
-        if (desc) atomicAdd(cnt + kCnDescents, desc);
+    block_add2(cnt, kCnBadRange, bad, kCnDescents, desc);
+}
+
+// the same counts from 16-byte loads (colidx 16-byte aligned): quad q holds positions 4q .. 4q+3,
+// the descent at 4q+3 compares with the next quad's first entry; the last nnz mod 4 positions go
+// to the first threads of the grid.  Each thread keeps four quads in flight.
+__global__ void k_check_elems4(const int4* __restrict__ colidx4, const int32_t* __restrict__ colidx,
+                               int64_t nnz, int32_t n, unsigned long long* cnt)
+{
+    constexpr int U = 4;
+    unsigned long long bad = 0, desc = 0;
+    const int64_t nq = nnz >> 2;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q0 = t0; q0 < nq; q0 += U * stride) {
+        int4 v[U];
+        int32_t nx[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t q = q0 + u * stride;
+            if (q < nq) {
+                v[u] = __ldg(colidx4 + q);
+                nx[u] = 4 * q + 4 < nnz ? __ldg(colidx + 4 * q + 4) : INT32_MAX;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (q0 + u * stride < nq) {
+                const int4 w = v[u];
+                bad += (w.x < 0 || w.x >= n) + (w.y < 0 || w.y >= n) + (w.z < 0 || w.z >= n) +
+                       (w.w < 0 || w.w >= n);
+                desc += (w.y <= w.x) + (w.z <= w.y) + (w.w <= w.z) + (nx[u] <= w.w);
+            }
+        }
     }
+    if (t0 < nnz - 4 * nq) {
+        const int64_t p = 4 * nq + t0;
+        const int32_t c = __ldg(colidx + p);
+        bad += (c < 0 || c >= n);
+        if (p + 1 < nnz) desc += (__ldg(colidx + p + 1) <= c);
+    }
+    block_add2(cnt, kCnBadRange, bad, kCnDescents, desc);
 }
 
 __global__ void k_check_rows(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
@@ -63,35 +125,61 @@ __global__ void k_check_rows(const int32_t* __restrict__ rowptr, const int32_t* 
         }
         bad += !ok;
     }
-    bad = warp_sum(bad);
-    sdesc = warp_sum(sdesc);
-    if ((threadIdx.x & 31) == 0) {
-        if (bad) atomicAdd(cnt + kCnBadPtr, bad);
-        if (sdesc) atomicAdd(cnt + kCnStartDescents, sdesc);
-    }
-}
-
-// rowptr entries clamped into [0, nnz] and made non-decreasing locally, so that later planner
-// kernels stay in bounds even before the validation result is read back.
-__device__ __forceinline__ int64_t clamp_ptr(const int32_t* rowptr, int64_t i, int64_t nnz)
-{
-    int64_t r = __ldg(rowptr + i);
-    return r < 0 ? 0 : (r > nnz ? nnz : r);
+    block_add2(cnt, kCnBadPtr, bad, kCnStartDescents, sdesc);
 }
 
 // ---------------------------------------------------------------------------------------------
-// residual row list when no window exists: every row, merge start = rowptr[i] + i
+// chunk rows: chunk_k0[c] = the residual-list row holding merge item c*W, c in [0, nc).  Row k
+// holds items [rl_start[k], rl_start[k+1]), so it owns the multiples of W in that range: written
+// row-parallel, without searches.  (rl_start strictly increases for valid inputs; the consumer
+// clamps what an invalid one leaves unwritten.)
 // ---------------------------------------------------------------------------------------------
-__global__ void k_rl_all_rows(const int32_t* __restrict__ rowptr, int32_t m, int64_t nnz,
-                              int32_t* rl_rows, int32_t* rl_start)
+__device__ __forceinline__ void own_chunk_rows(int64_t k, int64_t s, int64_t e, int64_t W, int64_t nc,
+                                               int32_t* chunk_k0)
 {
+    int64_t c = s > 0 ? (s + W - 1) / W : 0;
+    const int64_t ce = e > 0 ? (e + W - 1) / W : 0;
+    for (; c < ce && c < nc; ++c) chunk_k0[c] = (int32_t)k;
+}
+
+__global__ void k_chunk_rows(const int32_t* __restrict__ rl_start, int64_t n_rl, int64_t W, int64_t nc,
+                             int32_t* chunk_k0)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_rl;
+         k += (int64_t)gridDim.x * blockDim.x)
+        own_chunk_rows(k, __ldg(rl_start + k), __ldg(rl_start + k + 1), W, nc, chunk_k0);
+}
+
+// ---------------------------------------------------------------------------------------------
+// the all-residual plan in one row-parallel pass: the row checks of a1, the residual row list
+// (every row, merge start rowptr[i] + i), no split rows yet, and the chunk rows
+// ---------------------------------------------------------------------------------------------
+__global__ void k_rows_all_residual(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                    int32_t m, int64_t nnz, int64_t W, int64_t nc,
+                                    unsigned long long* cnt, int32_t* rl_rows, int32_t* rl_start,
+                                    int32_t* row_split, int32_t* chunk_k0)
+{
+    unsigned long long bad = 0, sdesc = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= m;
          i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < m) rl_rows[i] = (int32_t)i;
-        int64_t r = clamp_ptr(rowptr, i, nnz);
-        if (i == m) r = nnz;
-        rl_start[i] = (int32_t)(r + i);
+        const int64_t r = __ldg(rowptr + i);
+        bool ok = r >= 0 && r <= nnz;
+        if (i == 0 && r != 0) ok = false;
+        if (i == m && r != nnz) ok = false;
+        const int64_t rc = i == m ? nnz : (r < 0 ? 0 : (r > nnz ? nnz : r));
+        rl_start[i] = (int32_t)(rc + i);
+        if (i < m) {
+            const int64_t r1 = __ldg(rowptr + i + 1);
+            if (r1 < r) ok = false;
+            if (ok && r1 > r && r > 0 && r < nnz) sdesc += (__ldg(colidx + r) <= __ldg(colidx + r - 1));
+            rl_rows[i] = (int32_t)i;
+            row_split[i] = -1;
+            const int64_t r1c = i + 1 == m ? nnz : (r1 < 0 ? 0 : (r1 > nnz ? nnz : r1));
+            own_chunk_rows(i, rc + i, r1c + i + 1, W, nc, chunk_k0);
+        }
+        bad += !ok;
     }
+    block_add2(cnt, kCnBadPtr, bad, kCnStartDescents, sdesc);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -99,33 +187,38 @@ __global__ void k_rl_all_rows(const int32_t* __restrict__ rowptr, int32_t m, int
 // item falls in a residual row with 2*(len+1) <= W, in which case it moves to the row's start.
 // rl_start must be non-decreasing (guaranteed for valid inputs; clamped otherwise).
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ int64_t chunk_boundary(const int32_t* __restrict__ rl_start, int64_t n_rl,
-                                                  int64_t T, int64_t W, int64_t nc, int64_t c)
+__device__ __forceinline__ int64_t chunk_boundary(const int32_t* __restrict__ rl_start, int64_t T,
+                                                  int64_t W, int64_t nc, int64_t c, int64_t k)
 {
     if (c == 0) return 0;
     if (c >= nc) return T;
-    const int64_t d = c * W;
-    const int64_t k = upper_minus_one(rl_start, n_rl, d);
+    const int64_t d = c * W;  // merge item c*W lies in row k
     const int64_t rlen = (int64_t)__ldg(rl_start + k + 1) - __ldg(rl_start + k) - 1;
     return (2 * (rlen + 1) <= W) ? (int64_t)__ldg(rl_start + k) : d;
 }
 
 // also the execution-side chunk records: rows k0 .. kL with an item in [b0, b1) (row kL + 1
 // starts at or after b1), and the nonzero count = items - row ends inside the range (rows
-// k0 .. kL - 1 end inside it, row kL when its end item precedes b1)
+// k0 .. kL - 1 end inside it, row kL when its end item precedes b1).  chunk_k0 (from the chunk
+// rows pass) is the row of merge item c*W, which is also the row of the snapped boundary b0.
 __global__ void k_chunks(const int32_t* __restrict__ rl_start, const int32_t* __restrict__ rl_rows,
                          const int32_t* __restrict__ res_rowptr, int64_t m, int64_t n_rl, int64_t T,
-                         int64_t W, int64_t nc, int32_t* chunk_b, int32_t* chunk_k0, ChunkRec* rec)
+                         int64_t W, int64_t nc, int32_t* chunk_b, const int32_t* __restrict__ chunk_k0,
+                         ChunkRec* rec)
 {
+    auto row_of = [&](int64_t c) -> int64_t {
+        const int64_t k = __ldg(chunk_k0 + c);
+        return k < 0 ? 0 : (k >= n_rl ? n_rl - 1 : k);
+    };
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= nc;
          c += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = chunk_boundary(rl_start, n_rl, T, W, nc, c);
+        const int64_t k0 = c < nc ? row_of(c) : 0;
+        const int64_t b = chunk_boundary(rl_start, T, W, nc, c, k0);
         chunk_b[c] = (int32_t)b;
         if (c < nc) {
-            const int64_t k0 = upper_minus_one(rl_start, n_rl, b);
-            chunk_k0[c] = (int32_t)k0;
-            const int64_t b1 = chunk_boundary(rl_start, n_rl, T, W, nc, c + 1);
-            int64_t kL = (c + 1 < nc) ? upper_minus_one(rl_start, n_rl, b1) : n_rl - 1;
+            const int64_t k1 = (c + 1 < nc) ? row_of(c + 1) : n_rl - 1;
+            const int64_t b1 = chunk_boundary(rl_start, T, W, nc, c + 1, k1);
+            int64_t kL = k1;
             if (kL > k0 && (int64_t)__ldg(rl_start + kL) >= b1) --kL;
             ChunkRec r;
             r.b0 = (int32_t)b;
@@ -134,7 +227,7 @@ __global__ void k_chunks(const int32_t* __restrict__ rl_start, const int32_t* __
             r.kL = (int32_t)kL;
             r.total = -1;
             r.z0 = -1;
-            if (k0 >= 0 && kL >= k0 && kL < n_rl) {
+            if (kL >= k0) {
                 r.total = (int32_t)((b1 - b) - (kL - k0) - ((int64_t)__ldg(rl_start + kL + 1) <= b1 ? 1 : 0));
                 const int64_t i0 = __ldg(rl_rows + k0);
                 if (i0 >= 0 && i0 < m) r.z0 = (int32_t)((int64_t)__ldg(res_rowptr + i0) + (b - __ldg(rl_start + k0)));
@@ -205,6 +298,62 @@ struct PieceStore {
         split_np[s] = np;
         split_slot[s] = (int32_t)(pre & 0xffffffffLL);
         split_base[s] = base;
+    }
+};
+
+// All-residual plans have no dense windows, so a row is split only where chunk boundaries cut
+// it, and only a long row (2 * (len + 1) > W) can be cut: the boundaries inside it are the
+// unsnapped multiples of W.  Boundary c (1 <= c < nc) is the first cut of its row k when it lies
+// strictly inside the row and boundary c - 1 does not; the row's pieces then run from chunk c - 1
+// to the chunk of its end item, floor((e - 1) / W).  Scanning the nc - 1 boundaries instead of
+// the rows finds the same split rows in the same (ascending) order.
+struct CutInfo {
+    const int32_t* rl_rows;
+    const int32_t* rl_start;
+    const int32_t* chunk_k0;
+    int64_t n_rl;
+    int64_t nc;
+    int64_t W;
+    // the row that boundary c cuts first, or -1; its piece count in *np
+    __device__ __forceinline__ int64_t first_cut(int64_t c, int32_t* np) const
+    {
+        int64_t k = __ldg(chunk_k0 + c);
+        k = k < 0 ? 0 : (k >= n_rl ? n_rl - 1 : k);
+        const int64_t s = __ldg(rl_start + k), e = __ldg(rl_start + k + 1);
+        if (2 * (e - s) <= W || c * W <= s || (c - 1) * W > s) return -1;
+        int64_t lc = (e - 1) / W;
+        if (lc > nc - 1) lc = nc - 1;
+        *np = (int32_t)(lc - (c - 1) + 1);
+        return k;
+    }
+};
+struct CutLoad {  // item j is boundary j + 1
+    CutInfo ci;
+    __device__ __forceinline__ int64_t operator()(int64_t j) const
+    {
+        int32_t np = 0;
+        return ci.first_cut(j + 1, &np) >= 0 ? ((int64_t)1 << 32) | (int64_t)np : 0;
+    }
+};
+struct CutStore {
+    CutInfo ci;
+    int32_t* row_split;
+    int32_t* split_row;
+    int32_t* split_np;
+    int32_t* split_slot;
+    int32_t* split_base;
+    __device__ __forceinline__ void operator()(int64_t j, int64_t pre, int64_t v) const
+    {
+        if (v == 0) return;
+        int32_t np = 0;
+        const int64_t k = ci.first_cut(j + 1, &np);
+        const int32_t i = __ldg(ci.rl_rows + k);
+        const int64_t sp = pre >> 32;
+        row_split[i] = (int32_t)sp;
+        split_row[sp] = i;
+        split_np[sp] = np;
+        split_slot[sp] = (int32_t)(pre & 0xffffffffLL);
+        split_base[sp] = (int32_t)j;  // chunk c - 1
     }
 };
 
@@ -363,26 +512,34 @@ static ns_status_t splits_and_queue(Plan* P, const WindowResult* W, cudaStream_t
     const int64_t Wn = P->tune.chunk_nnz;
 
     if (nc > 0) {
+        if (W) {  // the all-residual plan wrote the chunk rows in its rows pass
+            k_chunk_rows<<<grid_for(n_rl), 256, 0, s>>>(P->rl_start, n_rl, Wn, nc, P->chunk_k0);
+            NS_LAUNCH_CHECK();
+        }
         k_chunks<<<grid_for(nc + 1), 256, 0, s>>>(P->rl_start, P->rl_rows, P->res_rowptr, m, n_rl, T, Wn, nc,
                                                    P->chunk_b, P->chunk_k0, P->chunk_rec);
         NS_LAUNCH_CHECK();
     } else {
         NS_CUDA_TRY(cudaMemsetAsync(P->chunk_b, 0, sizeof(int32_t), s));
     }
-    if (m > 0) {
+    if (W && m > 0) {  // (the all-residual rows pass filled it)
         k_fill_i32<<<grid_for(m), 256, 0, s>>>(P->row_split, m, -1);
         NS_LAUNCH_CHECK();
     }
     Arena tmp;
     int64_t* partial = nullptr;
     int32_t* hist = nullptr;
-    tmp.reserve(&partial, scan_partials(n_rl));
+    tmp.reserve(&partial, scan_partials(W ? n_rl : nc));
     tmp.reserve(&hist, bucket_hist_size(P->st.n_items));
     NS_TRY(tmp.commit(s));
-    if (n_rl > 0 && nc > 0) {
-        PieceInfo pi{P->rl_rows, P->rl_start, P->chunk_b, W ? W->row_state : nullptr, nc, Wn};
+    if (n_rl > 0 && nc > 0 && W) {
+        PieceInfo pi{P->rl_rows, P->rl_start, P->chunk_b, W->row_state, nc, Wn};
         PieceStore st{pi, P->row_split, P->split_row, P->split_np, P->split_slot, P->split_base};
         NS_TRY(device_scan<int64_t>(PieceLoad{pi}, st, n_rl, partial, totals, s));
+    } else if (n_rl > 0 && nc > 0) {
+        CutInfo ci{P->rl_rows, P->rl_start, P->chunk_k0, n_rl, nc, Wn};
+        CutStore st{ci, P->row_split, P->split_row, P->split_np, P->split_slot, P->split_base};
+        NS_TRY((device_scan<int64_t, CutLoad, CutStore, 1>(CutLoad{ci}, st, nc - 1, partial, totals, s)));
     }
     if (P->st.n_items > 0) {
         k_item_costs<<<grid_for(P->st.n_items), 256, 0, s>>>(P->chunk_b, nc, P->tune.group,
@@ -463,15 +620,20 @@ ns_status_t plan_build(Plan* P, const ns_csr_t* A, int32_t K, ns_dtype_t dt, con
         NS_CUDA_TRY(cudaMemsetAsync(totals, 0, sizeof(int64_t) * 16, s));
     }
 
-    // ---- a1: validation ----
+    // ---- a1: validation (the row half runs in the all-residual rows pass when there are no windows) ----
+    const bool windows_on = tune->tau_tile != kTauInf && m > 0;
     if (nnz > 0) {
-        k_check_elems<<<grid_for(nnz), 256, 0, s>>>(P->colidx, nnz, (int32_t)n, counters);
+        if (((uintptr_t)P->colidx & 15) == 0)
+            k_check_elems4<<<grid_for(nnz / 16 + 1), 256, 0, s>>>((const int4*)P->colidx, P->colidx, nnz,
+                                                                 (int32_t)n, counters);
+        else
+            k_check_elems<<<grid_for(nnz), 256, 0, s>>>(P->colidx, nnz, (int32_t)n, counters);
         NS_LAUNCH_CHECK();
     }
-    k_check_rows<<<grid_for(m + 1), 256, 0, s>>>(P->rowptr, P->colidx, (int32_t)m, nnz, counters);
-    NS_LAUNCH_CHECK();
-
-    const bool windows_on = tune->tau_tile != kTauInf && m > 0;
+    if (windows_on) {
+        k_check_rows<<<grid_for(m + 1), 256, 0, s>>>(P->rowptr, P->colidx, (int32_t)m, nnz, counters);
+        NS_LAUNCH_CHECK();
+    }
     if (tune->tau_tile != kTauInf && (int64_t)tune->TM * K > 16384) {
         set_error("dense tiles need TM * K <= 16384 (TM=%d, K=%d); lower TM", tune->TM, K);
         return NS_ERR_UNSUPPORTED;
@@ -518,7 +680,9 @@ ns_status_t plan_build(Plan* P, const ns_csr_t* A, int32_t K, ns_dtype_t dt, con
         P->blocks.push_back(a.take());
     }
     if (!windows_on) {
-        k_rl_all_rows<<<grid_for(m + 1), 256, 0, s>>>(P->rowptr, (int32_t)m, nnz, P->rl_rows, P->rl_start);
+        k_rows_all_residual<<<grid_for(m + 1), 256, 0, s>>>(P->rowptr, P->colidx, (int32_t)m, nnz,
+                                                            tune->chunk_nnz, nc, counters, P->rl_rows,
+                                                            P->rl_start, P->row_split, P->chunk_k0);
         NS_LAUNCH_CHECK();
     }
     NS_TRY(splits_and_queue(P, windows_on ? &win : nullptr, s, totals));

@@ -11,7 +11,6 @@ namespace ns {
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;
 
 template <class T>
 __device__ __forceinline__ T warp_incl_scan(T v)
@@ -54,14 +53,14 @@ __device__ __forceinline__ T block_excl_scan(T v, T* total, T* smem /* NT/32 + 1
     return r;
 }
 
-template <class T, class Load>
+template <class T, class Load, int ITEMS>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Load load, int64_t n, T* partial)
 {
     __shared__ T sm[kScanThreads / 32 + 1];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    const int64_t base = (int64_t)blockIdx.x * (kScanThreads * ITEMS);
     T acc = 0;
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {
         int64_t i = base + (int64_t)j * kScanThreads + threadIdx.x;
         if (i < n) acc += load(i);
     }
@@ -87,51 +86,68 @@ __global__ void __launch_bounds__(1024) k_scan_partials(T* partial, int64_t nb, 
     if (threadIdx.x == 0 && total_out) *total_out = carry;
 }
 
-// thread-sequential items: thread t owns items base + t*kScanItems .. +kScanItems-1
-template <class T, class Load, class Store>
+// warp-striped items: warp w of the block owns 32 * ITEMS consecutive items, lane l item
+// j * 32 + l of them, so every load of the Load functor is coalesced.  Prefixes come from a warp
+// scan per item row, carried across rows, then across the block's warps.
+template <class T, class Load, class Store, int ITEMS>
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(Load load, Store store, int64_t n,
                                                             const T* partial)
 {
-    __shared__ T sm[kScanThreads / 32 + 1];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    T v[kScanItems];
-    T acc = 0;
+    constexpr int NW = kScanThreads / 32;
+    __shared__ T wsum[NW + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t wbase = (int64_t)blockIdx.x * (kScanThreads * ITEMS) + (int64_t)warp * (32 * ITEMS);
+    T v[ITEMS];
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        int64_t i = base + j;
+    for (int j = 0; j < ITEMS; ++j) {
+        const int64_t i = wbase + j * 32 + lane;
         v[j] = i < n ? load(i) : T(0);
-        acc += v[j];
     }
-    T tot;
-    T pre = block_excl_scan<T, kScanThreads>(acc, &tot, sm) + partial[blockIdx.x];
+    T ex[ITEMS];
+    T run = 0;
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        int64_t i = base + j;
-        if (i < n) store(i, pre, v[j]);
-        pre += v[j];
+    for (int j = 0; j < ITEMS; ++j) {
+        const T inc = warp_incl_scan(v[j]);
+        ex[j] = run + inc - v[j];
+        run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) wsum[warp] = run;
+    __syncthreads();
+    if (warp == 0) {
+        const T w = lane < NW ? wsum[lane] : T(0);
+        const T wi = warp_incl_scan(w);
+        if (lane < NW) wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    const T pre = wsum[warp] + partial[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const int64_t i = wbase + j * 32 + lane;
+        if (i < n) store(i, pre + ex[j], v[j]);
     }
 }
 
-// Scratch for device_scan: ceil(n / kScanTile) partials.
-inline int64_t scan_partials(int64_t n) { return ceil_div(n > 0 ? n : 1, kScanTile); }
+// Scratch for device_scan: one partial per kScanThreads items (enough for any items per thread).
+inline int64_t scan_partials(int64_t n) { return ceil_div(n > 0 ? n : 1, kScanThreads); }
 
 // Exclusive scan: store(i, prefix_i, value_i) for i in [0, n); *total_out (device) = sum.
 // The reduce pass sums items in a different grouping than the down pass, which is fine for
-// integers (exact).  `partial` needs scan_partials(n) elements.
-template <class T, class Load, class Store>
+// integers (exact).  ITEMS items per thread: 8 for cheap loads over long ranges, 1 where each
+// load is a chain of dependent reads over a short range (more threads hide the latency).
+template <class T, class Load, class Store, int ITEMS = kScanItems>
 ns_status_t device_scan(Load load, Store store, int64_t n, T* partial, T* total_out,
                         cudaStream_t s)
 {
-    const int64_t nb = scan_partials(n);
+    const int64_t nb = ceil_div(n > 0 ? n : 1, kScanThreads * ITEMS);
     if (n <= 0) {
         if (total_out) NS_CUDA_TRY(cudaMemsetAsync(total_out, 0, sizeof(T), s));
         return NS_OK;
     }
-    k_scan_reduce<T, Load><<<(unsigned)nb, kScanThreads, 0, s>>>(load, n, partial);
+    k_scan_reduce<T, Load, ITEMS><<<(unsigned)nb, kScanThreads, 0, s>>>(load, n, partial);
     NS_LAUNCH_CHECK();
     k_scan_partials<T><<<1, 1024, 0, s>>>(partial, nb, total_out);
     NS_LAUNCH_CHECK();
-    k_scan_down<T, Load, Store><<<(unsigned)nb, kScanThreads, 0, s>>>(load, store, n, partial);
+    k_scan_down<T, Load, Store, ITEMS><<<(unsigned)nb, kScanThreads, 0, s>>>(load, store, n, partial);
     NS_LAUNCH_CHECK();
     return NS_OK;
 }

@@ -503,7 +503,7 @@ ns_status_t plan_check_tune(const ns_tune_t& t)
 // ---------------------------------------------------------------------------------------------
 // orchestration
 // ---------------------------------------------------------------------------------------------
-static ns_status_t splits_and_queue(Plan* P, const WindowResult* W, cudaStream_t s, int64_t* totals)
+static ns_status_t chunks_and_splits(Plan* P, const WindowResult* W, cudaStream_t s, int64_t* totals)
 {
     const int64_t m = P->st.m;
     const int64_t n_rl = P->st.n_rl;
@@ -528,9 +528,7 @@ static ns_status_t splits_and_queue(Plan* P, const WindowResult* W, cudaStream_t
     }
     Arena tmp;
     int64_t* partial = nullptr;
-    int32_t* hist = nullptr;
     tmp.reserve(&partial, scan_partials(W ? n_rl : nc));
-    tmp.reserve(&hist, bucket_hist_size(P->st.n_items));
     NS_TRY(tmp.commit(s));
     if (n_rl > 0 && nc > 0 && W) {
         PieceInfo pi{P->rl_rows, P->rl_start, P->chunk_b, W->row_state, nc, Wn};
@@ -541,16 +539,44 @@ static ns_status_t splits_and_queue(Plan* P, const WindowResult* W, cudaStream_t
         CutStore st{ci, P->row_split, P->split_row, P->split_np, P->split_slot, P->split_base};
         NS_TRY((device_scan<int64_t, CutLoad, CutStore, 1>(CutLoad{ci}, st, nc - 1, partial, totals, s)));
     }
-    if (P->st.n_items > 0) {
-        k_item_costs<<<grid_for(P->st.n_items), 256, 0, s>>>(P->chunk_b, nc, P->tune.group,
-                                                              P->st.n_dwin, W ? W->dcost : nullptr,
-                                                              P->st.n_items, P->tune.cost_res,
-                                                              P->item_cost);
-        NS_LAUNCH_CHECK();
-        NS_TRY(bucket_sort_desc(CostKey{P->item_cost}, QueueEmit{P->queue}, P->st.n_items, hist, s));
-    }
     tmp.release(s);
     return NS_OK;
+}
+
+static ns_status_t work_queue(Plan* P, const WindowResult* W, cudaStream_t s)
+{
+    if (P->st.n_items <= 0) return NS_OK;
+    Arena tmp;
+    int32_t* hist = nullptr;
+    tmp.reserve(&hist, bucket_hist_size(P->st.n_items));
+    NS_TRY(tmp.commit(s));
+    k_item_costs<<<grid_for(P->st.n_items), 256, 0, s>>>(P->chunk_b, P->st.n_chunks, P->tune.group,
+                                                          P->st.n_dwin, W ? W->dcost : nullptr,
+                                                          P->st.n_items, P->tune.cost_res, P->item_cost);
+    NS_LAUNCH_CHECK();
+    NS_TRY(bucket_sort_desc(CostKey{P->item_cost}, QueueEmit{P->queue}, P->st.n_items, hist, s));
+    tmp.release(s);
+    return NS_OK;
+}
+
+// Pinned host words for the planner's readbacks, one buffer per host thread (plans may be built
+// from several threads at once).  A device-to-host copy into pageable memory returns only after
+// the stream has drained, so pinned words let the host wait on an event instead while the GPU
+// goes on with the work queue.  nullptr when pinned memory is unavailable.
+constexpr int kReadbackWords = 24;  // 8 validation counters + 16 totals
+static unsigned long long* readback_words()
+{
+    thread_local unsigned long long* buf = nullptr;
+    thread_local bool tried = false;
+    if (!tried) {
+        tried = true;
+        if (cudaHostAlloc(reinterpret_cast<void**>(&buf), kReadbackWords * sizeof(unsigned long long), 0) !=
+            cudaSuccess) {
+            (void)cudaGetLastError();
+            buf = nullptr;
+        }
+    }
+    return buf;
 }
 
 static ns_status_t report_invalid(const unsigned long long* hc)
@@ -649,8 +675,10 @@ ns_status_t plan_build(Plan* P, const ns_csr_t* A, int32_t K, ns_dtype_t dt, con
         P->res_val = P->vals;
     } else {
         // the window kernels read row contents: validation must pass first
-        unsigned long long hc[8];
-        NS_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof hc, cudaMemcpyDeviceToHost, s));
+        unsigned long long hc_own[8];
+        unsigned long long* rb = readback_words();
+        unsigned long long* hc = rb ? rb : hc_own;
+        NS_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost, s));
         NS_CUDA_TRY(cudaStreamSynchronize(s));
         if (!csr_ok(hc)) return report_invalid(hc);
         NS_TRY(window_pass(P, &win, s));  // sets m_aic .. T and the residual / window arrays
@@ -685,7 +713,28 @@ ns_status_t plan_build(Plan* P, const ns_csr_t* A, int32_t K, ns_dtype_t dt, con
                                                             P->rl_start, P->row_split, P->chunk_k0);
         NS_LAUNCH_CHECK();
     }
-    NS_TRY(splits_and_queue(P, windows_on ? &win : nullptr, s, totals));
+    const WindowResult* W = windows_on ? &win : nullptr;
+    NS_TRY(chunks_and_splits(P, W, s, totals));
+
+    // ---- one readback (validation counters and split totals), overlapped with the work queue ----
+    unsigned long long hbuf[kReadbackWords];
+    unsigned long long* rb = readback_words();
+    unsigned long long* hc = rb ? rb : hbuf;
+    int64_t* ht = reinterpret_cast<int64_t*>(hc + 8);
+    struct EventGuard {
+        cudaEvent_t e = nullptr;
+        ~EventGuard()
+        {
+            if (e) cudaEventDestroy(e);
+        }
+    } ev;
+    if (rb) {
+        NS_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost, s));
+        NS_CUDA_TRY(cudaMemcpyAsync(ht, totals, sizeof(int64_t) * 16, cudaMemcpyDeviceToHost, s));
+        NS_CUDA_TRY(cudaEventCreateWithFlags(&ev.e, cudaEventDisableTiming));
+        NS_CUDA_TRY(cudaEventRecord(ev.e, s));
+    }
+    NS_TRY(work_queue(P, W, s));
 
     // ---- hot B rows for the L2 policy (l2_hints == 2) ----
     if (tune->l2_hints == 2 && n > 0) {
@@ -720,12 +769,13 @@ ns_status_t plan_build(Plan* P, const ns_csr_t* A, int32_t K, ns_dtype_t dt, con
         h.release(s);
     }
 
-    // ---- one readback: validation counters and split totals ----
-    unsigned long long hc[8];
-    int64_t ht[16];
-    NS_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof hc, cudaMemcpyDeviceToHost, s));
-    NS_CUDA_TRY(cudaMemcpyAsync(ht, totals, sizeof ht, cudaMemcpyDeviceToHost, s));
-    NS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (ev.e) {
+        NS_CUDA_TRY(cudaEventSynchronize(ev.e));
+    } else {
+        NS_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost, s));
+        NS_CUDA_TRY(cudaMemcpyAsync(ht, totals, sizeof(int64_t) * 16, cudaMemcpyDeviceToHost, s));
+        NS_CUDA_TRY(cudaStreamSynchronize(s));
+    }
     if (win.temp.ptr) {
         NS_CUDA_TRY(cudaFreeAsync(win.temp.ptr, s));
         win.temp = DevBlock{};

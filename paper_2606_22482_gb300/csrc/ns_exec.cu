@@ -62,35 +62,44 @@ __device__ __forceinline__ float ld_stream_f32(const float* p, uint64_t pol)
     return v;
 }
 
-// four consecutive B elements (16 B of FP32 or 8 B of BF16) widened to float
+// Four consecutive B elements as loaded: 16 B of FP32 or 8 B of BF16.  Rings of gathers keep
+// this raw form and widen a vector only where it is used: a conversion next to its load would
+// wait for the load there and leave one gather in flight instead of the ring's depth.
+template <bool BF16>
+using BRaw = std::conditional_t<BF16, uint2, float4>;
+
 template <bool BF16, bool HINT>
-__device__ __forceinline__ float4 ld_b4(const void* B, int64_t off, uint64_t pol)
+__device__ __forceinline__ BRaw<BF16> ld_braw(const void* p, uint64_t pol)
 {
-    float4 r;
-    if (!BF16) {
-        const float* p = reinterpret_cast<const float*>(B) + off;
+    BRaw<BF16> r;
+    if constexpr (!BF16) {
         if (HINT)
             asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
                          : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p), "l"(pol));
         else
             r = __ldg(reinterpret_cast<const float4*>(p));
     } else {
-        const uint16_t* p = reinterpret_cast<const uint16_t*>(B) + off;
-        uint32_t a, b;
         if (HINT)
             asm volatile("ld.global.nc.L2::cache_hint.v2.b32 {%0,%1}, [%2], %3;"
-                         : "=r"(a), "=r"(b) : "l"(p), "l"(pol));
-        else {
-            uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-            a = u.x;
-            b = u.y;
-        }
-        r.x = __uint_as_float(a << 16);
-        r.y = __uint_as_float(a & 0xffff0000u);
-        r.z = __uint_as_float(b << 16);
-        r.w = __uint_as_float(b & 0xffff0000u);
+                         : "=r"(r.x), "=r"(r.y) : "l"(p), "l"(pol));
+        else
+            r = __ldg(reinterpret_cast<const uint2*>(p));
     }
     return r;
+}
+
+template <bool BF16>
+__device__ __forceinline__ BRaw<BF16> braw_zero()
+{
+    if constexpr (BF16) return make_uint2(0u, 0u);
+    else return make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ float4 widen(const float4& v) { return v; }
+__device__ __forceinline__ float4 widen(const uint2& v)  // BF16 is the high half of an FP32
+{
+    return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u),
+                       __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
 }
 
 template <bool HINT>
@@ -206,20 +215,22 @@ __device__ __forceinline__ void gather_accumulate(const ExecDesc& D, int64_t z0,
                 val[u] = __shfl_sync(0xffffffffu, mv, j & 31);
                 if (j >= cnt) val[u] = 0.f, col[u] = -1;
             }
-            float4 b[4][VPL];
+            BRaw<BF16> b[4][VPL];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int q = 0; q < VPL; ++q) {
-                    int v = li + L * q;
+                    const int v = li + L * q;
+                    const int64_t off = (int64_t)col[u] * D.ldb + 4 * v;
                     b[u][q] = (col[u] >= 0 && v < nv)
-                                  ? ld_b4<BF16, HINT>(D.B, (int64_t)col[u] * D.ldb + 4 * v, pol.last)
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                                  ? ld_braw<BF16, HINT>(static_cast<const unsigned char*>(D.B) +
+                                                            off * (BF16 ? 2 : 4), pol.last)
+                                  : braw_zero<BF16>();
                 }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(val[u], b[u][q], acc[q]);
+                for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(val[u], widen(b[u][q]), acc[q]);
         }
     }
 }
@@ -400,9 +411,9 @@ __device__ __forceinline__ void stream_rows(const ExecDesc& D, int32_t c, int la
     };
 
     constexpr int U = VPL == 1 ? kRing : kRing / 2;
-    float4 b[U][VPL];
+    BRaw<BF16> b[U][VPL];
     float w[U];
-    auto gather = [&](int2 e, float4 (&dst)[VPL], float& wv) {
+    auto gather = [&](int2 e, BRaw<BF16> (&dst)[VPL], float& wv) {
         // padding entries point at a real row with value 0: no test needed here.  With the hot
         // map, bit 31 of the column id marks a hot row (set when the chunk was decoded).
         const uint32_t col = HOT ? ((uint32_t)e.x & 0x7fffffffu) : (uint32_t)e.x;
@@ -411,8 +422,8 @@ __device__ __forceinline__ void stream_rows(const ExecDesc& D, int32_t c, int la
         if (HOT) pl = e.x < 0 ? pol.last : pol.first;
 #pragma unroll
         for (int q = 0; q < VPL; ++q) {
-            if (FULL || lane + 32 * q < nv) dst[q] = ld_b4<BF16, HINT>(row + 32 * VB * q, 0, pl);
-            else dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (FULL || lane + 32 * q < nv) dst[q] = ld_braw<BF16, HINT>(row + 32 * VB * q, pl);
+            else dst[q] = braw_zero<BF16>();
         }
         wv = __int_as_float(e.y);
     };
@@ -425,7 +436,7 @@ __device__ __forceinline__ void stream_rows(const ExecDesc& D, int32_t c, int la
             while (P >= next_end) flush();
             const int2 e = ent[P + U];
 #pragma unroll
-            for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], b[u][q], acc[q]);
+            for (int q = 0; q < VPL; ++q) acc[q] = f4_fma(w[u], widen(b[u][q]), acc[q]);
             gather(e, b[u], w[u]);
         }
     }
@@ -764,7 +775,7 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     float4 acc[VPL];
 #pragma unroll
     for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 b[ASYNC ? 1 : kR][VPL];
+    BRaw<BF16> b[ASYNC ? 1 : kR][VPL];
     float w[kR];
     auto gather = [&](int2 e, int u) {
         const uint32_t col = HOT ? ((uint32_t)e.x & 0x7fffffffu) : (uint32_t)e.x;
@@ -776,15 +787,15 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
         } else {
 #pragma unroll
             for (int q = 0; q < VPL; ++q) {
-                if (FULL || li + 32 * q < nv) b[u][q] = ld_b4<BF16, HINT>(row + 32 * VB * q, 0, pl);
-                else b[u][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (FULL || li + 32 * q < nv) b[u][q] = ld_braw<BF16, HINT>(row + 32 * VB * q, pl);
+                else b[u][q] = braw_zero<BF16>();
             }
         }
         w[u] = __int_as_float(e.y);
     };
     auto bvec = [&](int u, int q) -> float4 {
         if constexpr (ASYNC) return aring[u * 32 + lane];
-        else return b[u][q];
+        else return widen(b[u][q]);
     };
     // step u of a group covers entries P + u EPS + g; the ring's first kR steps
 #pragma unroll
@@ -908,13 +919,15 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     __syncwarp();  // the batch ring is reused by this warp's next chunk
 }
 
-template <int VPL, int EPS, bool BF16, bool HINT>
+// SMEM_RING: the FP32 one-vector form may stage its gathers in the shared-memory cp.async ring
+// (pays off when the gathered rows come from DRAM; when B sits in L2 the register ring is faster)
+template <int VPL, int EPS, bool BF16, bool HINT, bool SMEM_RING = true>
 __global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : 5) k_exec_contig(
     const ExecDesc* __restrict__ descs, const int32_t* __restrict__ queue,
     const int32_t* __restrict__ queue_desc, int64_t n_items, int32_t* ctrl,
     const __grid_constant__ ExecDesc d0)
 {
-    constexpr bool ASYNC = VPL == 1 && EPS == 1 && !BF16;
+    constexpr bool ASYNC = SMEM_RING && VPL == 1 && EPS == 1 && !BF16;
     __shared__ float4 s_park[kExecWarps * 32 * VPL];  // one parked partial row per warp
     __shared__ float4 s_aring[ASYNC ? kExecWarps * 8 * 32 : 1];
     __shared__ int2 s_bat[kExecWarps * 128];          // per warp: 4 batches of 32 (col, value)
@@ -1040,20 +1053,24 @@ static ExecKernel pick_kernel(int K)
 
 // nonzeros per warp step: as many lane groups as the K/4 vectors of a row leave room for
 template <bool BF16, bool HINT>
-static ExecKernel pick_contig(int K)
+static ExecKernel pick_contig(int K, bool b_in_l2)
 {
     if (K <= 32) return k_exec_contig<1, 4, BF16, HINT>;
     if (K <= 64) return k_exec_contig<1, 2, BF16, HINT>;
+    if constexpr (!BF16)
+        if (K <= 128 && b_in_l2) return k_exec_contig<1, 1, BF16, HINT, false>;
     if (K <= 128) return k_exec_contig<1, 1, BF16, HINT>;
     return k_exec_contig<2, 1, BF16, HINT>;
 }
 
-// contig: a residual-only launch whose plans all have a contiguous residual stream (K <= 256)
-static ExecKernel select_kernel(int K, bool bf16, bool hint, bool dense, bool contig)
+// contig: 0, or a residual-only launch whose plans all have a contiguous residual stream
+// (K <= 256): kContig, or kContigBInL2 when B fits comfortably in L2
+static ExecKernel select_kernel(int K, bool bf16, bool hint, bool dense, int contig)
 {
     if (contig && !dense && K <= 256) {
-        if (bf16) return hint ? pick_contig<true, true>(K) : pick_contig<true, false>(K);
-        return hint ? pick_contig<false, true>(K) : pick_contig<false, false>(K);
+        const bool in_l2 = contig == kContigBInL2;
+        if (bf16) return hint ? pick_contig<true, true>(K, in_l2) : pick_contig<true, false>(K, in_l2);
+        return hint ? pick_contig<false, true>(K, in_l2) : pick_contig<false, false>(K, in_l2);
     }
     if (bf16) {
         if (hint) return dense ? pick_kernel<true, true, true>(K) : pick_kernel<true, true, false>(K);
@@ -1061,6 +1078,18 @@ static ExecKernel select_kernel(int K, bool bf16, bool hint, bool dense, bool co
     }
     if (hint) return dense ? pick_kernel<false, true, true>(K) : pick_kernel<false, true, false>(K);
     return dense ? pick_kernel<false, false, true>(K) : pick_kernel<false, false, false>(K);
+}
+
+int64_t l2_bytes(int device)
+{
+    static int cached[64] = {0};
+    if (device < 0 || device >= 64) return 0;
+    if (!cached[device]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, device) != cudaSuccess || v <= 0) v = 1;
+        cached[device] = v;
+    }
+    return cached[device];
 }
 
 int num_sms(int device)
@@ -1077,7 +1106,7 @@ int num_sms(int device)
 
 // dynamic shared memory of one execute CTA: the dense item's tiles (phase 1) or the residual
 // warps' staging rings (phase 2), whichever is larger
-static size_t exec_smem_bytes(int K, int TM, int TK, bool bf16, bool dense, int W, bool contig)
+static size_t exec_smem_bytes(int K, int TM, int TK, bool bf16, bool dense, int W, int contig)
 {
     if (contig && !dense && K <= 256) return 0;  // the contiguous-stream kernel keeps no staging
     // (L, VPL) exactly as pick_kernel chooses the instantiation
@@ -1096,7 +1125,7 @@ static size_t exec_smem_bytes(int K, int TM, int TK, bool bf16, bool dense, int 
 // Kernel attributes and the persistent grid (resident CTAs on every SM, at most n_items).
 // Must run outside stream capture.
 ns_status_t exec_prepare(int64_t n_items, int K, int TM, int TK, bool bf16, bool hint, bool dense,
-                         int* grid_out, int W, bool contig)
+                         int* grid_out, int W, int contig)
 {
     ExecKernel kern = select_kernel(K, bf16, hint, dense, contig);
     const size_t smem = exec_smem_bytes(K, TM, TK, bf16, dense, W, contig);
@@ -1119,7 +1148,7 @@ ns_status_t exec_prepare(int64_t n_items, int K, int TM, int TK, bool bf16, bool
 ns_status_t exec_launch(const ExecDesc* descs, const int32_t* queue, const int32_t* queue_desc,
                         int64_t n_items, int32_t* ctrl, int K, int TM, int TK, bool bf16, bool hint,
                         bool dense, int* grid_cache, cudaStream_t s, const ExecDesc* d0, int W,
-                        bool contig)
+                        int contig)
 {
     ExecKernel kern = select_kernel(K, bf16, hint, dense, contig);
     const size_t smem = exec_smem_bytes(K, TM, TK, bf16, dense, W, contig);
@@ -1143,9 +1172,15 @@ ns_status_t exec_launch_plan(Plan* P, cudaStream_t s)
         P->exec_grid_slice = 0;
         P->exec_grid_slice_K = K;
     }
+    int contig = 0;
+    if (plan_contig(P)) {
+        // B (this slice of it) within half of L2: the gathers hit L2, keep them in registers
+        const int64_t b_bytes = P->st.n * (int64_t)K * (P->dtype == NS_BF16 ? 2 : 4);
+        contig = 2 * b_bytes <= l2_bytes(P->device) ? kContigBInL2 : kContig;
+    }
     return exec_launch(nullptr, P->queue, nullptr, P->st.n_items, P->ctrl, K, P->tune.TM,
                        P->tune.TK, P->dtype == NS_BF16, P->tune.l2_hints != 0, P->st.n_dwin > 0,
-                       gc, s, &P->desc_host, P->tune.chunk_nnz, plan_contig(P));
+                       gc, s, &P->desc_host, P->tune.chunk_nnz, contig);
 }
 
 }  // namespace ns

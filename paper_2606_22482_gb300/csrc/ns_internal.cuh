@@ -224,6 +224,11 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s);
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int num_sms(int device);
+int64_t l2_bytes(int device);
+
+// residual-only launch modes of exec_launch / exec_prepare (`contig`)
+constexpr int kContig = 1;       // contiguous residual stream
+constexpr int kContigBInL2 = 2;  // the same, with B small enough to stay in L2
 
 // planner entry (ns_plan.cu)
 ns_status_t plan_build(Plan* P, const ns_csr_t* A, int32_t K, ns_dtype_t dt, const ns_tune_t* tune,
@@ -235,10 +240,10 @@ void fill_desc(const Plan* P, const void* B, int64_t ldb, float* C, int64_t ldc,
 ns_status_t exec_launch(const ExecDesc* descs, const int32_t* queue, const int32_t* queue_desc,
                         int64_t n_items, int32_t* ctrl, int K, int TM, int TK, bool bf16, bool hint,
                         bool dense, int* grid_cache, cudaStream_t s, const ExecDesc* d0 = nullptr,
-                        int W = 256, bool contig = false);
+                        int W = 256, int contig = 0);
 ns_status_t exec_launch_plan(Plan* P, cudaStream_t s);
 ns_status_t exec_prepare(int64_t n_items, int K, int TM, int TK, bool bf16, bool hint, bool dense,
-                         int* grid_out, int W = 256, bool contig = false);
+                         int* grid_out, int W = 256, int contig = 0);
 bool plan_contig(const Plan* P);  // contiguous residual stream (tau_tile = inf)
 ns_status_t plan_create(const ns_csr_t* A, int32_t K, ns_dtype_t dt, const ns_tune_t* tune,
                         cudaStream_t s, Plan** out);  // checks + build; on error nothing is kept

@@ -89,6 +89,14 @@ def test_attention_full(dtype, tol):
     check(A, B, dtype, tune_from(ns, tau_tile=128, TM=16, TK=16), tol)
 
 
+@pytest.mark.parametrize("dtype,tol", [(ns.NS_F32, 1e-5), (ns.NS_BF16, 2e-2)])
+def test_attention_residual_full(dtype, tol):
+    # all of A on the CUDA cores; B (16 MiB) fits in L2, so the FP32 form gathers through the
+    # register ring rather than the shared-memory ring the power-law B (512 MiB) takes
+    A, B = synth.config_attention(0)
+    check(A, B, dtype, tune_from(ns, tau_tile=ns.NS_TAU_INF), tol)
+
+
 def test_small_config_full():
     A, B = synth.config_small(0)
     C = check(A, B, ns.NS_F32, ns.tune_default(), 1e-5)

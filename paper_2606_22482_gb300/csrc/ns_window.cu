@@ -227,7 +227,6 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
 {
     __shared__ int64_t rb[kMaxTM + 1];   // run boundaries (relative to wbase)
     __shared__ int64_t rb0[kMaxTM + 1];  // original row boundaries
-    __shared__ int32_t skeys[2][kWinSmemKeys];
     __shared__ int64_t sscan[kWinThreads / 32 + 1];
     __shared__ int32_t wc[kWinThreads / 32][kMaxTM + 1];
     __shared__ int32_t binoff[kMaxTM + 1];
@@ -252,6 +251,8 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
     int32_t* ucnt = a.ucnt + wbase;
     int32_t* upos = a.upos + wbase;
     // ---- unique columns of the window in ascending order, with their counts ----
+    // Dynamic shared memory: the column counters and positions of the counting path, or (the
+    // other path) the two key buffers of an in-shared-memory sort; a CTA takes one of the two.
     extern __shared__ uint32_t dyn_cols[];
     const bool count_cols = a.count_cols && N > kWinSmemKeys;  // window-uniform
     const int nwords = (a.n + 3) >> 2;
@@ -273,35 +274,60 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
         }
         if (threadIdx.x == 0) s_carry[0] = 0;
         __syncthreads();
-        // compaction in ascending column order
-        for (int q0 = 0; q0 < nwords; q0 += blockDim.x) {
-            const int q = q0 + threadIdx.x;
-            const uint32_t wv = q < nwords ? dyn_cols[q] : 0u;
-            int64_t f = 0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) f += ((wv >> (8 * b)) & 0xffu) ? 1 : 0;
-            int64_t tot;
-            int64_t pre = block_excl_scan<int64_t, kWinThreads>(f, &tot, sscan) + s_carry[0];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const uint32_t cnt = (wv >> (8 * b)) & 0xffu;
-                if (cnt) {
-                    uasc[pre] = 4 * q + b;
-                    ucnt[pre] = (int32_t)cnt;
-                    cpos[4 * q + b] = (uint16_t)pre;
-                    ++pre;
+        // compaction in ascending column order: warp w owns a segment of the words, counts its
+        // columns, the segments' counts are scanned once, and each warp then emits its segment
+        // 32 words at a time with a warp scan (no block barrier per step)
+        {
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            const int seg = (((nwords + nw - 1) / nw) + 31) & ~31;
+            const int wlo = warp * seg, whi = wlo + seg < nwords ? wlo + seg : nwords;
+            auto present = [](uint32_t wv) {
+                return (int)((wv & 0xffu) != 0) + (int)((wv & 0xff00u) != 0) + (int)((wv & 0xff0000u) != 0) +
+                       (int)((wv & 0xff000000u) != 0);
+            };
+            int cnt = 0;
+            for (int q = wlo + lane; q < whi; q += 32) cnt += present(dyn_cols[q]);
+            cnt = warp_sum(cnt);
+            if (lane == 0) sscan[warp] = cnt;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int64_t acc = 0;
+                for (int q = 0; q < nw; ++q) {
+                    const int64_t c = sscan[q];
+                    sscan[q] = acc;
+                    acc += c;
                 }
+                s_carry[0] = acc;
             }
             __syncthreads();
-            if (threadIdx.x == 0) s_carry[0] += tot;
+            int64_t base = sscan[warp];
+            for (int q0 = wlo; q0 < whi; q0 += 32) {
+                const int q = q0 + lane;
+                const uint32_t wv = q < whi ? dyn_cols[q] : 0u;
+                const int f = present(wv);
+                const int inc = warp_incl_scan(f);
+                int64_t pre = base + inc - f;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const uint32_t c = (wv >> (8 * b)) & 0xffu;
+                    if (c) {
+                        uasc[pre] = 4 * q + b;
+                        ucnt[pre] = (int32_t)c;
+                        cpos[4 * q + b] = (uint16_t)pre;
+                        ++pre;
+                    }
+                }
+                base += __shfl_sync(0xffffffffu, inc, 31);
+            }
             __syncthreads();
         }
     } else {
         // sort the window's columns (merge of sorted row segments), then run-length encode;
         // start positions go to upos (temporary)
         const bool in_smem = N <= kWinSmemKeys;
-        int32_t* b0 = in_smem ? skeys[0] : a.sortbuf0 + wbase;
-        int32_t* b1 = in_smem ? skeys[1] : a.sortbuf1 + wbase;
+        int32_t* const skeys = reinterpret_cast<int32_t*>(dyn_cols);
+        int32_t* b0 = in_smem ? skeys : a.sortbuf0 + wbase;
+        int32_t* b1 = in_smem ? skeys + kWinSmemKeys : a.sortbuf1 + wbase;
         for (int64_t e = threadIdx.x; e < N; e += blockDim.x) b0[e] = a.ekey[wbase + e];
         __syncthreads();
         const int32_t* sorted = cta_merge_runs(b0, b1, N, rb, nrows);
@@ -981,12 +1007,15 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
         WinArgs wa{P->rowptr, aic_rows, row_kbase, ekey, m_aic, TM, TK, t.tau_tile, t.col_order,
                    sb0, sb1, uasc, ucnt, upos, ucan, ccnt, trank, tvoff, epos,
                    win_U, win_ndt, win_ndv, win_res, res_len, (int32_t)n, count_cols ? 1 : 0};
-        const size_t dyn = count_cols ? (size_t)3 * (((n + 3) / 4) * 4) : 0;
+        // the counting table (3 bytes a column) or the two sort buffers, whichever is larger
+        const size_t tbl = count_cols ? (size_t)3 * (((n + 3) / 4) * 4) : 0;
+        const size_t keys = (size_t)2 * kWinSmemKeys * sizeof(int32_t);
+        const size_t dyn = tbl > keys ? tbl : keys;
         // static + dynamic shared memory above 48 KB needs the opt-in; one fixed limit (the largest
         // counting table) keeps concurrent planners from lowering it under each other's launches
-        if (dyn > 0)
-            NS_CUDA_TRY(cudaFuncSetAttribute(k_window_compact, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             3 * kDenseCols));
+        static_assert(3 * kDenseCols >= 2 * kWinSmemKeys * 4, "sort buffers fit the opt-in limit");
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_window_compact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         3 * kDenseCols));
         k_window_compact<<<(unsigned)n_win, kWinThreads, dyn, s>>>(wa);
         NS_LAUNCH_CHECK();
     }

@@ -88,6 +88,19 @@ __device__ __forceinline__ BRaw<BF16> ld_braw(const void* p, uint64_t pol)
     return r;
 }
 
+// 16 raw bytes (eight BF16 columns)
+template <bool HINT>
+__device__ __forceinline__ uint4 ld_b16(const void* p, uint64_t pol)
+{
+    uint4 r;
+    if (HINT)
+        asm volatile("ld.global.nc.L2::cache_hint.v4.b32 {%0,%1,%2,%3}, [%4], %5;"
+                     : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p), "l"(pol));
+    else
+        r = __ldg(reinterpret_cast<const uint4*>(p));
+    return r;
+}
+
 template <bool BF16>
 __device__ __forceinline__ BRaw<BF16> braw_zero()
 {
@@ -250,7 +263,8 @@ __device__ __forceinline__ void group_reduce(float4 (&acc)[VPL])
 }
 
 // split-row delivery out of line (rare): keeps the inlined row flush of the stream path small
-template <int VPL, bool HINT>
+// PAIR: the lane holds vectors 2 lane and 2 lane + 1 (adjacent), otherwise lane and lane + 32
+template <int VPL, bool HINT, bool PAIR = false>
 __device__ __noinline__ void deliver_split_row(const ExecDesc& D, int32_t row, int32_t s, int32_t c,
                                                float4 a0, float4 a1, int lane, uint64_t pol_first)
 {
@@ -258,9 +272,9 @@ __device__ __noinline__ void deliver_split_row(const ExecDesc& D, int32_t row, i
     const int32_t np = __ldg(D.split_np + s);
     const int32_t piece = c - __ldg(D.split_base + s);
     float* slot0 = D.slots + (int64_t)__ldg(D.split_slot + s) * D.K;
-    if (lane < nv) __stcg(reinterpret_cast<float4*>(slot0 + (int64_t)piece * D.K + 4 * lane), a0);
-    if (VPL > 1 && lane + 32 < nv)
-        __stcg(reinterpret_cast<float4*>(slot0 + (int64_t)piece * D.K + 4 * (lane + 32)), a1);
+    const int v0 = PAIR ? 2 * lane : lane, v1 = PAIR ? 2 * lane + 1 : lane + 32;
+    if (v0 < nv) __stcg(reinterpret_cast<float4*>(slot0 + (int64_t)piece * D.K + 4 * v0), a0);
+    if (VPL > 1 && v1 < nv) __stcg(reinterpret_cast<float4*>(slot0 + (int64_t)piece * D.K + 4 * v1), a1);
     __threadfence();
     __syncwarp();
     int old = 0;
@@ -271,7 +285,7 @@ __device__ __noinline__ void deliver_split_row(const ExecDesc& D, int32_t row, i
     float* crow = D.C + (int64_t)row * D.ldc;
 #pragma unroll
     for (int q = 0; q < VPL; ++q) {
-        const int v = lane + 32 * q;
+        const int v = PAIR ? 2 * lane + q : lane + 32 * q;
         if (v < nv) {
             float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int p = 0; p < np; ++p)
@@ -714,7 +728,10 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     // 16 bytes, so no warp barrier), which doubles the rows in flight without spending registers;
     // otherwise a kCRing-deep register ring.
     constexpr int kR = ASYNC ? 8 : kCRing;  // ring depth (steps in flight)
-    static_assert(EPS == 1 || VPL == 1, "several nonzeros per step only for K <= 128");
+    // PAIR (BF16, K <= 128): each lane gathers 8 adjacent columns (16 bytes, vectors 2 li and
+    // 2 li + 1), so 16 lanes cover a row and the warp takes two nonzeros per step
+    constexpr bool PAIR = BF16 && VPL == 2 && EPS == 2;
+    static_assert(EPS == 1 || VPL == 1 || PAIR, "several nonzeros per step only for K <= 128");
     constexpr int G = 32 / EPS;
     const int g = lane / G, li = lane % G;
     const int4 h0 = __ldg(reinterpret_cast<const int4*>(D.chunk_rec + c));
@@ -728,7 +745,8 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     }
     const int nv = D.K >> 2;
     constexpr int VB = BF16 ? 8 : 16;  // bytes of one 4-column vector
-    const unsigned char* const Bl = reinterpret_cast<const unsigned char*>(D.B) + VB * li;
+    const unsigned char* const Bl = reinterpret_cast<const unsigned char*>(D.B) + (PAIR ? 2 : 1) * VB * li;
+    auto vidx = [&](int q) { return PAIR ? 2 * li + q : li + 32 * q; };  // vector q of this lane
     const uint32_t ldb_bytes = (uint32_t)(D.ldb * (BF16 ? 2 : 4));
 
     // ---- batches of 32 (col, value) pairs; past the end: the last column again with value 0 ----
@@ -775,7 +793,8 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     float4 acc[VPL];
 #pragma unroll
     for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    BRaw<BF16> b[ASYNC ? 1 : kR][VPL];
+    using Raw = std::conditional_t<PAIR, uint4, BRaw<BF16>>;
+    Raw b[ASYNC ? 1 : kR][PAIR ? 1 : VPL];
     float w[kR];
     auto gather = [&](int2 e, int u) {
         const uint32_t col = HOT ? ((uint32_t)e.x & 0x7fffffffu) : (uint32_t)e.x;
@@ -784,6 +803,9 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
         if constexpr (ASYNC) {
             cp_async16<HINT>(aring + u * 32 + lane, row, FULL || li < nv, pl);
             cp_async_commit();
+        } else if constexpr (PAIR) {  // K a multiple of 8: both vectors valid or neither
+            if (FULL || 2 * li < nv) b[u][0] = ld_b16<HINT>(row, pl);
+            else b[u][0] = make_uint4(0u, 0u, 0u, 0u);
         } else {
 #pragma unroll
             for (int q = 0; q < VPL; ++q) {
@@ -795,7 +817,10 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
     };
     auto bvec = [&](int u, int q) -> float4 {
         if constexpr (ASYNC) return aring[u * 32 + lane];
-        else return widen(b[u][q]);
+        else if constexpr (PAIR) {
+            const uint4 v = b[u][0];
+            return q == 0 ? widen(make_uint2(v.x, v.y)) : widen(make_uint2(v.z, v.w));
+        } else return widen(b[u][q]);
     };
     // step u of a group covers entries P + u EPS + g; the ring's first kR steps
 #pragma unroll
@@ -823,7 +848,7 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
         float* crow = D.C + (int64_t)(k0 + r) * D.ldc;
 #pragma unroll
         for (int q = 0; q < VPL; ++q) {
-            const int v = li + 32 * q;
+            const int v = vidx(q);
             if (g == 0 && (FULL || v < nv)) st_c4<HINT>(crow + 4 * v, acc[q], pol.first);
         }
     };
@@ -905,14 +930,15 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
         float4 p[VPL];
 #pragma unroll
         for (int q = 0; q < VPL; ++q) p[q] = park[32 * q + lane];
-        deliver_split_row<VPL, HINT>(D, k0, __ldg(D.row_split + k0), c, p[0], p[VPL > 1 ? VPL - 1 : 0], lane,
-                                     pol.first);
+        deliver_split_row<VPL, HINT, PAIR>(D, k0, __ldg(D.row_split + k0), c, p[0], p[VPL > 1 ? VPL - 1 : 0],
+                                           lane, pol.first);
     }
     while (r < nr) {  // rows ending at or after the last nonzero (and the last row)
         const int32_t sp = __shfl_sync(0xffffffffu, wsplit, r & 31);
         if (EPS > 1) reduce_groups();
         if (sp < 0) store_row();
-        else deliver_split_row<VPL, HINT>(D, k0 + r, sp, c, acc[0], acc[VPL > 1 ? VPL - 1 : 0], lane, pol.first);
+        else deliver_split_row<VPL, HINT, PAIR>(D, k0 + r, sp, c, acc[0], acc[VPL > 1 ? VPL - 1 : 0], lane,
+                                                pol.first);
         advance();
     }
     if constexpr (ASYNC) cp_async_wait<0>();  // the look-ahead copies land before the ring is reused
@@ -922,7 +948,7 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
 // SMEM_RING: the FP32 one-vector form may stage its gathers in the shared-memory cp.async ring
 // (pays off when the gathered rows come from DRAM; when B sits in L2 the register ring is faster)
 template <int VPL, int EPS, bool BF16, bool HINT, bool SMEM_RING = true>
-__global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : 5) k_exec_contig(
+__global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : (EPS == 2 ? 6 : 5)) k_exec_contig(
     const ExecDesc* __restrict__ descs, const int32_t* __restrict__ queue,
     const int32_t* __restrict__ queue_desc, int64_t n_items, int32_t* ctrl,
     const __grid_constant__ ExecDesc d0)
@@ -1057,8 +1083,11 @@ static ExecKernel pick_contig(int K, bool b_in_l2)
 {
     if (K <= 32) return k_exec_contig<1, 4, BF16, HINT>;
     if (K <= 64) return k_exec_contig<1, 2, BF16, HINT>;
-    if constexpr (!BF16)
+    if constexpr (BF16) {
+        if (K <= 128) return k_exec_contig<2, 2, BF16, HINT>;  // 8 columns a lane, 2 nonzeros a step
+    } else {
         if (K <= 128 && b_in_l2) return k_exec_contig<1, 1, BF16, HINT, false>;
+    }
     if (K <= 128) return k_exec_contig<1, 1, BF16, HINT>;
     return k_exec_contig<2, 1, BF16, HINT>;
 }

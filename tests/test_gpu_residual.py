@@ -70,6 +70,17 @@ def test_chunk_sizes_split_rows(W):
     assert oracle.rel_frobenius(c, ref) <= 1e-6
 
 
+@pytest.mark.parametrize("K", [72, 96, 128])
+@pytest.mark.parametrize("W", [16, 512])
+def test_bf16_paired_widths(K, W):
+    # BF16 with 64 < K <= 128: each lane gathers 8 adjacent columns and the warp takes two
+    # nonzeros per step; W = 16 cuts the hub rows into pieces assembled through the slots
+    A = synth.random_csr(300, 500, 0.05, seed=K + W, hub_rows=4, empty_rows=0.2)
+    B = synth.dense_b(500, K, seed=3)
+    c, ref = run(A, B, ns.NS_BF16, tune=tune_from(ns, chunk_nnz=W, absorb_cap=W))
+    assert oracle.rel_frobenius(c, ref) <= 1e-6
+
+
 def test_identity_and_permutation_exact():
     A = synth.identity_csr(3000)
     B = synth.dense_b(3000, 64, seed=3)

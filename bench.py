@@ -112,9 +112,9 @@ class ClockSampler:
 EXEC_SOURCES = ("ns_exec.cu", "ns_internal.cuh", "ns_dense.cuh", "ns_ptx.cuh")
 MEASURED_TRAFFIC = {
     # (workload, tau_tile, chunk_nnz, l2_hints): (source digest, bytes per launch)
-    ("powerlaw", 2147483647, 512, 1): ("8c2f8cdf7316ffda", 1676326912 + 541956096),
-    ("powerlaw", 2147483647, 256, 1): ("8c2f8cdf7316ffda", 1698592512 + 586521856),
-    ("powerlaw", 2147483647, 1024, 1): ("8c2f8cdf7316ffda", 1670348288 + 530667520),
+    ("powerlaw", 2147483647, 512, 1): ("92ae39a35c43ac30", 1676669184 + 541900032),
+    ("powerlaw", 2147483647, 256, 1): ("92ae39a35c43ac30", 1698748416 + 586447872),
+    ("powerlaw", 2147483647, 1024, 1): ("92ae39a35c43ac30", 1671091712 + 530661120),
 }
 
 

@@ -456,6 +456,15 @@ def bench_batched(args, threads):
     except Exception as e:
         tune = ns.tune_default()
         src = f"default ({str(e)[:40]})"
+    if args.chunk is not None:
+        tune.chunk_nnz = tune.absorb_cap = args.chunk
+        src += f", W={args.chunk} by flag"
+    else:
+        try:  # W timed on the whole batch (untimed tuning, like the dry runs above)
+            tune, _ = ns.batch_autotune(Ad, [K] * len(graphs), ns.NS_F32, Bd, Cd, start=tune)
+            src += f", W={tune.chunk_nnz} timed on the whole batch"
+        except Exception as e:
+            src += f" (batch W sweep unavailable: {str(e)[:40]})"
     t0 = time.perf_counter()
     bt = ns.Batch(Ad, [K] * len(graphs), ns.NS_F32, tune)
     plan_s = time.perf_counter() - t0

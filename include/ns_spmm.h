@@ -173,6 +173,16 @@ ns_status_t ns_batch_execute(ns_batch_t b, const void* const* Bs, float* const* 
 ns_status_t ns_batch_stats(ns_batch_t b, int64_t* n_items, int64_t* n_graphs);
 ns_status_t ns_batch_destroy(ns_batch_t b);
 
+/* The residual chunk size W (chunk_nnz, with absorb_cap = W) for a whole batch: each W in
+ * {128, 256, 512, 1024} is planned as a batch from `start` (NULL: defaults) and its launch is
+ * timed on Bs / Cs (device pointers as in ns_batch_execute; Cs is overwritten); *out gets start
+ * with the fastest W and *best_ms (may be NULL) its launch time.  The best W of one graph alone
+ * (ns_autotune) can differ from the batch's, where many small chunks share one launch.
+ * Synchronous; errors as ns_batch_plan / ns_batch_execute. */
+ns_status_t ns_batch_autotune(const ns_csr_t* As, int32_t count, const int32_t* Ks, ns_dtype_t b_dtype,
+                              const ns_tune_t* start, const void* const* Bs, float* const* Cs,
+                              ns_stream_t s, ns_tune_t* out, double* best_ms);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Autotuner (Section 5.2.1 dry run + Section 8 sweeps).                                     */
 /* ---------------------------------------------------------------------------------------- */

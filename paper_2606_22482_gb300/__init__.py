@@ -17,6 +17,7 @@ from ._abi import (NS_F32, NS_BF16, NS_TAU_INF, NsError, Tune, PlanStats, lib, c
 
 __all__ = ["NS_F32", "NS_BF16", "NS_TAU_INF", "NsError", "Tune", "PlanStats", "Plan", "rebalance",
            "spmm_plan", "spmm_execute", "spmm_host", "tune_default", "launch_count", "lib",
+           "batch_autotune",
            "PLAN_ARRAYS"]
 
 PLAN_ARRAYS = ("aic_rows", "win_rows", "win_dptr", "dwin", "dwin_absorb", "dtile_cols",
@@ -191,6 +192,26 @@ def rebalance(A: dict, K: int, b_dtype: int, B, C, start: Tune | None = None, ep
               "dt_tc_ms": list(rep.dt_tc_ms[:n]), "dt_res_ms": list(rep.dt_res_ms[:n]),
               "skew": list(rep.skew[:n])}
     return out, report
+
+
+def batch_autotune(As: list, Ks: list, b_dtype: int, Bs: list, Cs: list, start: Tune | None = None,
+                   stream=None) -> tuple:
+    """ns_batch_autotune: the chunk size W timed on the whole batch; returns (Tune, best_ms)."""
+    structs, keep = [], []
+    for A in As:
+        c, k = _csr_struct(A, True)
+        structs.append(c)
+        keep.append(k)
+    arr = (_abi.Csr * len(structs))(*structs)
+    ks = (ctypes.c_int32 * len(Ks))(*[int(k) for k in Ks])
+    bp = (ctypes.c_void_p * len(Bs))(*[b.data_ptr() for b in Bs])
+    cp = (ctypes.c_void_p * len(Cs))(*[c.data_ptr() for c in Cs])
+    out = Tune()
+    ms = ctypes.c_double()
+    check(lib.ns_batch_autotune(arr, len(structs), ks, int(b_dtype),
+                                ctypes.byref(start) if start is not None else None, bp, cp,
+                                _stream_handle(stream), ctypes.byref(out), ctypes.byref(ms)))
+    return out, ms.value
 
 
 class Batch:

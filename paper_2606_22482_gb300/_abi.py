@@ -87,6 +87,9 @@ SIGNATURES = {
     "ns_batch_execute": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.POINTER(P), P]),
     "ns_batch_stats": (ctypes.c_int, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
     "ns_batch_destroy": (ctypes.c_int, [P]),
+    "ns_batch_autotune": (ctypes.c_int, [ctypes.POINTER(Csr), I32, ctypes.POINTER(I32), I32, ctypes.POINTER(Tune),
+                                         ctypes.POINTER(P), ctypes.POINTER(P), P, ctypes.POINTER(Tune),
+                                         ctypes.POINTER(ctypes.c_double)]),
     "ns_autotune": (ctypes.c_int, [ctypes.POINTER(Csr), I32, I32, P, ctypes.POINTER(Tune), ctypes.POINTER(TuneReport)]),
     "ns_cost_alpha": (D, [D, D, D]),
     "ns_cost_tau": (I32, [D, I32, I32]),

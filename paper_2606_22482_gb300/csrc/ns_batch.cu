@@ -272,6 +272,71 @@ ns_status_t ns_batch_destroy(ns_batch_t b)
     return NS_OK;
 }
 
+// The residual chunk size W of the whole batch: every candidate is planned as a batch and its
+// launch timed (best of three replays after a warm one), the rest of the tune kept.
+ns_status_t ns_batch_autotune(const ns_csr_t* As, int32_t count, const int32_t* Ks, ns_dtype_t b_dtype,
+                              const ns_tune_t* start, const void* const* Bs, float* const* Cs,
+                              ns_stream_t s, ns_tune_t* out, double* best_ms)
+{
+    if (!As || count <= 0 || !Ks || !Bs || !Cs || !out) {
+        set_error("NULL argument or empty batch");
+        return NS_ERR_INVALID;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(s);
+    ns_tune_t base;
+    if (start) base = *start;
+    else ns_tune_default(&base);
+    const int32_t Ws[4] = {128, 256, 512, 1024};
+    ns_tune_t best = base;
+    double best_t = 1e300;
+    cudaEvent_t e0, e1;
+    NS_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        set_error("cudaEventCreate failed");
+        return NS_ERR_CUDA;
+    }
+    ns_status_t r = NS_OK;
+    for (int32_t w : Ws) {
+        ns_tune_t t = base;
+        t.chunk_nnz = w;
+        t.absorb_cap = w;
+        ns_batch_t b = nullptr;
+        r = ns_batch_plan(As, count, Ks, b_dtype, &t, s, &b);
+        if (r == NS_ERR_UNSUPPORTED || r == NS_ERR_INVALID) {  // this W does not apply; try the next
+            r = NS_OK;
+            continue;
+        }
+        if (r != NS_OK) break;
+        double t_best = 1e300;
+        for (int rep = 0; rep < 4 && r == NS_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            r = ns_batch_execute(b, Bs, Cs, s);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) r = NS_ERR_CUDA;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < t_best) t_best = ms;  // the first replay captures the graph
+        }
+        ns_batch_destroy(b);
+        if (r != NS_OK) break;
+        if (t_best < best_t) {
+            best_t = t_best;
+            best = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != NS_OK) return r;
+    if (best_t >= 1e300) {
+        set_error("no chunk size applies to this batch");
+        return NS_ERR_UNSUPPORTED;
+    }
+    *out = best;
+    if (best_ms) *best_ms = best_t;
+    return NS_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // autotuner
 // ---------------------------------------------------------------------------------------------

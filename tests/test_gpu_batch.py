@@ -48,6 +48,26 @@ def test_batch_matches_oracle_and_replays(tau):
     bt.close()
 
 
+def test_batch_autotune_picks_a_chunk_size():
+    graphs = synth.batch_graphs(12, seed=9, n_lo=300, n_hi=5000)
+    K = 64
+    rng = np.random.default_rng(3)
+    Bs = [rng.standard_normal((g["n"], K), dtype=np.float32) for g in graphs]
+    Ad = [to_dev(g, DEV) for g in graphs]
+    Bd = [torch.from_numpy(b).to(DEV) for b in Bs]
+    Cd = [torch.empty((g["m"], K), device=DEV) for g in graphs]
+    start = tune_from(ns, TM=32)
+    t, ms = ns.batch_autotune(Ad, [K] * len(graphs), ns.NS_F32, Bd, Cd, start=start)
+    assert t.chunk_nnz in (128, 256, 512, 1024) and t.absorb_cap == t.chunk_nnz
+    assert t.TM == 32 and ms > 0                       # the rest of the start tune is kept
+    bt = ns.Batch(Ad, [K] * len(graphs), ns.NS_F32, t)
+    bt.execute(Bd, Cd)
+    torch.cuda.synchronize()
+    for g, b, c in zip(graphs, Bs, Cd):
+        assert oracle.rel_frobenius(c.cpu().numpy(), oracle.spmm(g, b)) <= 1e-5
+    bt.close()
+
+
 def test_batch_mixed_K():
     graphs = synth.batch_graphs(6, seed=7, n_lo=300, n_hi=3000)
     Ks = [32, 64, 32, 128, 64, 32]

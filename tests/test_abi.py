@@ -52,3 +52,21 @@ def test_cost_helpers_match_closed_forms(ns):
         assert ns.lib.ns_cost_tau(a, tm, tk) == F.tau_tile(a, tm, tk)
     assert ns.lib.ns_skew(2.0, 1.0) == F.skew(2.0, 1.0)
     assert ns.lib.ns_skew(1.0, 3.0) == F.skew(1.0, 3.0)
+
+
+def test_argument_errors_without_a_device(ns):
+    # entry points reject missing arguments before any CUDA call, with a message
+    import ctypes
+    lib = ns.lib
+    assert lib.ns_spmm_plan(None, 32, ns.NS_F32, None, None, None) == 1      # NS_ERR_INVALID
+    assert b"NULL" in lib.ns_last_error()
+    assert lib.ns_batch_autotune(None, 0, None, ns.NS_F32, None, None, None, None, None, None) == 1
+    assert lib.ns_plan_destroy(None) == 0
+    t = ns.tune_default()
+    t.TM = 24                                                              # not 16, 32 or 64
+    c = ns._abi.Csr(4, 4, 0, None, None, None, 1)
+    rp = (ctypes.c_int32 * 5)()
+    c.rowptr = ctypes.cast(rp, ctypes.c_void_p)
+    h = ctypes.c_void_p()
+    assert lib.ns_spmm_plan(ctypes.byref(c), 32, ns.NS_F32, ctypes.byref(t), None, ctypes.byref(h)) == 1
+    assert b"tune" in lib.ns_last_error()

@@ -512,7 +512,7 @@ static ns_status_t chunks_and_splits(Plan* P, const WindowResult* W, cudaStream_
     const int64_t Wn = P->tune.chunk_nnz;
 
     if (nc > 0) {
-        if (W) {  // the all-residual plan wrote the chunk rows in its rows pass
+        if (W) {  // plans with windows; the all-residual plan wrote the chunk rows in its rows pass
             k_chunk_rows<<<grid_for(n_rl), 256, 0, s>>>(P->rl_start, n_rl, Wn, nc, P->chunk_k0);
             NS_LAUNCH_CHECK();
         }
@@ -522,7 +522,7 @@ static ns_status_t chunks_and_splits(Plan* P, const WindowResult* W, cudaStream_
     } else {
         NS_CUDA_TRY(cudaMemsetAsync(P->chunk_b, 0, sizeof(int32_t), s));
     }
-    if (W && m > 0) {  // (the all-residual rows pass filled it)
+    if (W && m > 0) {  // no split rows yet (the all-residual rows pass did this itself)
         k_fill_i32<<<grid_for(m), 256, 0, s>>>(P->row_split, m, -1);
         NS_LAUNCH_CHECK();
     }

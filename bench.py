@@ -49,7 +49,11 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons, sampled every 20 ms.  The sampler is started and
+    has delivered its first sample before the timed region begins (`with` entry waits for it);
+    `summary()` keeps the samples that arrived between `start()` and `stop()` (a sample arrives
+    a few ms after it is taken), or, for a region shorter than the interval, the first sample
+    after `start()`."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -58,23 +62,34 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (arrival time, line)
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            deadline = time.perf_counter() + 5.0
+            while not self.lines and time.perf_counter() < deadline and self.proc.poll() is None:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def start(self):
+        self.t0 = time.perf_counter()
+
+    def stop(self):
+        self.t1 = time.perf_counter()
+        time.sleep(0.05)  # let the samples taken inside the region arrive
 
     def __exit__(self, *exc):
         if self.proc:
@@ -85,9 +100,16 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        rows = self.lines
+        if self.t0 is not None and self.t1 is not None:
+            inside = [ln for t, ln in rows if self.t0 <= t <= self.t1 + 0.03]
+            after = [ln for t, ln in rows if t >= self.t0][:1]
+            picked = inside or after
+        else:
+            picked = [ln for _, ln in rows]
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in picked:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -207,7 +229,7 @@ def dist_env():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="powerlaw",
@@ -357,11 +379,13 @@ def main():
     torch.cuda.synchronize()
     launches0 = ns.launch_count()
     with ClockSampler(local) as clk:
+        clk.start()
         t_start.record(stream)
         for i in range(args.steps):
             step(exec_events[i])
         t_end.record(stream)
         torch.cuda.synchronize()
+        clk.stop()
     launches = ns.launch_count() - launches0
     if ws > 1:
         dist.barrier()
@@ -475,11 +499,13 @@ def bench_batched(args, threads):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = ns.launch_count()
     with ClockSampler(0) as clk:
+        clk.start()
         e0.record(stream)
         for _ in range(args.steps):
             bt.execute(Bd, Cd)
         e1.record(stream)
         torch.cuda.synchronize()
+        clk.stop()
     ms = e0.elapsed_time(e1) / args.steps
     # parity on a sample of graphs
     errs = []
@@ -540,11 +566,13 @@ def bench_gcn(args, threads):
     torch.cuda.synchronize()
     l0 = ns.launch_count()
     with ClockSampler(0) as clk:
+        clk.start()
         ev[2].record(stream)
         for _ in range(args.epochs):
             out = net.forward(Xt)
         ev[3].record(stream)
         torch.cuda.synchronize()
+        clk.stop()
     ms_epoch = ev[2].elapsed_time(ev[3]) / args.epochs
     launches = ns.launch_count() - l0
     # the SpMM part alone (same plan, same operands)

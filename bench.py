@@ -219,6 +219,19 @@ def run_cpu_oracle(A, B, K, seconds_budget: float, threads: int, bf16: bool = Fa
                       f"FP64, {dt:.1f} s"}
 
 
+def replicas_result(ms_step: float, flops_per_rank: float, ws: int, device) -> tuple:
+    """Whole-job step time and throughput of `ws` independent replicas (no data-path collective):
+    the slowest rank's step time (max over ranks) and all ranks' flops over it, in GFLOP/s.
+    Every rank calls it; with ws > 1 the process group must be initialised."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    return ms_step, flops_per_rank * ws / (ms_step * 1e-3) / 1e9
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -392,13 +405,9 @@ def main():
     ms_total = t_start.elapsed_time(t_end)
     exec_ms = float(np.mean([a.elapsed_time(b) for a, b in exec_events]))
     ms_step = ms_total / args.steps
-    if ws > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
 
     flops = 2.0 * A.nnz * K
-    value = flops * ws / (ms_step * 1e-3) / 1e9
+    ms_step, value = replicas_result(ms_step, flops, ws, dev)
     hbm, peak_src = _peaks()
     alg_bytes, n_touched = algorithmic_bytes(A, K, 2 if bf16 else 4)
     achieved = alg_bytes / (exec_ms * 1e-3) / 1e9

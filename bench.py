@@ -37,6 +37,8 @@ sys.path.insert(0, ROOT)
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
+# the headline metric, printed identically by both arms
+METRIC = "SpMM GFLOP/s (2*nnz*K/s) & % HBM roofline"
 
 
 def _peaks():
@@ -195,13 +197,46 @@ def cpu_sample_rows(A, target_nnz: int, seed: int = 7):
     rng = np.random.default_rng(seed)
     m = A["m"]
     frac = min(1.0, target_nnz / max(A.nnz, 1))
+    if frac >= 1.0:
+        return np.arange(m, dtype=np.int32), int(A.nnz)
     rows = np.nonzero(rng.random(m) < frac)[0].astype(np.int32)
     lens = np.diff(A["rowptr"].astype(np.int64))[rows]
     return rows, int(lens.sum())
 
 
-def run_cpu_oracle(A, B, K, seconds_budget: float, threads: int, bf16: bool = False):
-    """Time the oracle, as it stands, on a row sample sized for ~seconds_budget of CPU work."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), for the record beside the CPU baseline."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        fields = dict(ln.split(":", 1) for ln in out.splitlines() if ":" in ln)
+        name = fields.get("Model name", "").strip()
+        vendor = fields.get("Vendor ID", "").strip()
+        return f"{vendor} {name}".strip() or "unknown"
+    except Exception:
+        import platform
+        return platform.processor() or "unknown"
+
+
+def oracle_single_thread(A, B, K, bf16: bool, seconds_budget: float = 4.0) -> dict:
+    """The oracle on one host core, on a row sample sized for about seconds_budget."""
+    import oracle
+    rows, nnz_s = cpu_sample_rows(A, 100_000, seed=5)
+    t0 = time.perf_counter()
+    oracle.spmm(A, B, rows=rows, threads=1, b_bf16=bf16)
+    rate = 2.0 * nnz_s * K / max(time.perf_counter() - t0, 1e-9)
+    rows, nnz_s = cpu_sample_rows(A, int(rate * seconds_budget / (2.0 * K)), seed=13)
+    t0 = time.perf_counter()
+    oracle.spmm(A, B, rows=rows, threads=1, b_bf16=bf16)
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * nnz_s * K / dt / 1e9, "unit": "GFLOP/s", "cores": 1,
+            "sample": f"{len(rows)} uniformly sampled rows ({nnz_s} nnz, {nnz_s / A.nnz:.1%} of A), "
+                      f"FP64, {dt:.1f} s"}
+
+
+def run_cpu_oracle(A, B, K, seconds_budget: float, threads: int, bf16: bool = False, C_gpu=None):
+    """Time the oracle, as it stands, on all host cores: the whole matrix when that fits about
+    seconds_budget, else a uniform row sample of that size.  With C_gpu (the device result,
+    copied back after the timed region) the same oracle rows give its error against FP64."""
     import oracle
     rows, nnz_s = cpu_sample_rows(A, 200_000)
     t0 = time.perf_counter()
@@ -211,12 +246,23 @@ def run_cpu_oracle(A, B, K, seconds_budget: float, threads: int, bf16: bool = Fa
     target = int(min(A.nnz, max(200_000, rate * seconds_budget / (2.0 * K))))
     rows, nnz_s = cpu_sample_rows(A, target, seed=11)
     t0 = time.perf_counter()
-    oracle.spmm(A, B, rows=rows, threads=threads, b_bf16=bf16)
+    ref = oracle.spmm(A, B, rows=rows, threads=threads, b_bf16=bf16)
     dt = time.perf_counter() - t0
-    return {"value": 2.0 * nnz_s * K / dt / 1e9, "unit": "GFLOP/s", "cores": threads,
-            "kind": "oracle",
-            "sample": f"{len(rows)} uniformly sampled rows ({nnz_s} nnz, {nnz_s / A.nnz:.1%} of A), "
-                      f"FP64, {dt:.1f} s"}
+    out = {"value": 2.0 * nnz_s * K / dt / 1e9, "unit": "GFLOP/s", "cores": threads,
+           "kind": "oracle",
+           "sample": f"{len(rows)} rows ({nnz_s} nnz, {nnz_s / A.nnz:.1%} of A), FP64, {dt:.2f} s",
+           "cpu_model": cpu_model(),
+           "single_thread": oracle_single_thread(A, B, K, bf16)}
+    acc = None
+    if C_gpu is not None:
+        diff = np.asarray(C_gpu[rows], dtype=np.float64) - ref
+        dn, rn = np.linalg.norm(diff, axis=1), np.linalg.norm(ref, axis=1)
+        nz = rn > 0
+        acc = {"rel_frobenius_vs_fp64": float(np.linalg.norm(dn) / max(np.linalg.norm(rn), 1e-300)),
+               "max_row_rel_err": float((dn[nz] / rn[nz]).max()) if nz.any() else 0.0,
+               "zero_rows_exact": bool(np.all(dn[~nz] == 0)),
+               "rows_checked": int(len(rows)), "of_rows": int(A["m"])}
+    return out, acc
 
 
 def replicas_result(ms_step: float, flops_per_rank: float, ws: int, device) -> tuple:
@@ -275,25 +321,31 @@ def main():
             return
         A, B, desc = make_workload(args.workload, args.seed)
         K = B.shape[1]
-        times = []
+        bf16 = desc["b_dtype"] == "bf16"
         import oracle
-        rows, nnz_s = cpu_sample_rows(A, 300_000, seed=3)
+        if bf16:
+            import synth
+            B = synth.bf16_bits(B)
+        # every step is the whole matrix (the power-law graph takes about 0.2 s on 16 cores)
+        rows, nnz_s = cpu_sample_rows(A, A.nnz)
+        times = []
         for i in range(args.warmup + args.steps):
             t0 = time.perf_counter()
-            oracle.spmm(A, B, rows=rows, threads=threads)
+            oracle.spmm(A, B, rows=rows, threads=threads, b_bf16=bf16)
             dt = time.perf_counter() - t0
             if i >= args.warmup:
                 times.append(dt)
         t = float(np.mean(times))
         val = 2.0 * nnz_s * K / t / 1e9
-        sample = f"{len(rows)} uniformly sampled rows ({nnz_s} nnz) per step, FP64 oracle"
+        sample = f"the whole matrix ({len(rows)} rows, {nnz_s} nnz) per step, FP64 oracle"
         print(json.dumps({
-            "impl": "reference", "metric": "SpMM GFLOP/s (2*nnz*K/s)", "value": val,
+            "impl": "reference", "metric": METRIC, "value": val,
             "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": desc,
             "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": cpu_model(),
+                             "single_thread": oracle_single_thread(A, B, K, bf16)},
             "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }))
         return
@@ -435,11 +487,12 @@ def main():
         if ws > 1:
             dist.destroy_process_group()
         return
-    cpu = None
+    cpu = acc = None
     if not args.no_cpu:
-        cpu = run_cpu_oracle(A, B, K, 12.0, threads, bf16)
+        # the last timed step's C, read back after the timed region, against the FP64 oracle
+        cpu, acc = run_cpu_oracle(A, B, K, 12.0, threads, bf16, C_gpu=Ct.cpu().numpy())
     out = {
-        "metric": "SpMM GFLOP/s (2*nnz*K/s) & % HBM roofline",
+        "metric": METRIC,
         "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if bf16 else "f32", "data": "synthetic",
@@ -454,6 +507,8 @@ def main():
                      "kernel_ms": exec_ms, "frac_of_8000": achieved / 8000.0},
         "plan_ms": ms_step - exec_ms,
         "rebalance": rebalance_rep,
+        "rel_frobenius_vs_fp64": acc["rel_frobenius_vs_fp64"] if acc else None,
+        "accuracy": acc,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -516,10 +571,9 @@ def bench_batched(args, threads):
         torch.cuda.synchronize()
         clk.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    # parity on a sample of graphs
-    errs = []
-    for g in range(0, len(graphs), 37):
-        errs.append(oracle.rel_frobenius(Cd[g].cpu().numpy(), oracle.spmm(graphs[g], Bs[g], threads=threads)))
+    # every graph of the batch against the FP64 oracle (after the timed region)
+    errs = [oracle.rel_frobenius(Cd[g].cpu().numpy(), oracle.spmm(graphs[g], Bs[g], threads=threads))
+            for g in range(len(graphs))]
     n_touched = sum(int(np.count_nonzero(np.bincount(g["colidx"], minlength=g["n"]))) for g in graphs)
     alg = sum(4 * (g["m"] + 1) + 8 * g.nnz + 4 * g["m"] * K for g in graphs) + 4 * K * n_touched
     hbm, src_pk = _peaks()
@@ -533,7 +587,9 @@ def bench_batched(args, threads):
                    "tune": tune.as_dict(), "tune_source": src, "plan_s": plan_s, **bt.stats()},
         "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                      "frac": alg / (ms * 1e-3) / 1e9 / hbm, "traffic": None, "peak_source": src_pk},
-        "max_rel_frobenius_sampled": max(errs), "gpu_launches": ns.launch_count() - l0,
+        "rel_frobenius_vs_fp64": max(errs), "accuracy": {"max_rel_frobenius_per_graph": max(errs),
+                                                          "graphs_checked": len(errs)},
+        "gpu_launches": ns.launch_count() - l0,
         "clocks": clk.summary()}))
 
 
@@ -599,8 +655,7 @@ def bench_gcn(args, threads):
     XW2 = torch.matmul(H1, Ws[1])
     plan.execute(XW2, C)
     torch.cuda.synchronize()
-    rows = np.sort(np.random.default_rng(3).choice(A["m"], size=2000, replace=False)).astype(np.int32)
-    err = oracle.rel_frobenius(C.cpu().numpy()[rows], oracle.spmm(A, XW2.cpu().numpy(), rows=rows, threads=threads))
+    err = oracle.rel_frobenius(C.cpu().numpy(), oracle.spmm(A, XW2.cpu().numpy(), threads=threads))
     plan.close()
     nnz = A.nnz
     total_ms = plan_ms + args.epochs * ms_epoch
@@ -616,7 +671,8 @@ def bench_gcn(args, threads):
         "spmm_share_of_epoch": 2 * spmm_ms / ms_epoch,
         "plan_share_of_run": plan_ms / total_ms,
         "spmm_gflops": 2.0 * nnz * K / (spmm_ms * 1e-3) / 1e9,
-        "max_rel_frobenius_sampled": err, "gpu_launches": launches, "clocks": clk.summary()}))
+        "rel_frobenius_vs_fp64": err, "accuracy": {"spmm": "layer-2 SpMM, every row"},
+        "gpu_launches": launches, "clocks": clk.summary()}))
 
 
 # ---------------------------------------------------------------------------------------------
@@ -730,8 +786,9 @@ def bench_serve(args, threads):
                    "GFLOP_per_s": flops / wall_s / 1e9},
         "plain": {"requests_per_s": n_req / wall_p, "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
                   "GFLOP_per_s": flops / wall_p / 1e9, "how": "one request at a time, ns_spmm_host"},
-        "max_rel_frobenius": {"f32": max([e for e, b in errs if not b] or [0.0]),
-                              "bf16": max([e for e, b in errs if b] or [0.0])}}))
+        "rel_frobenius_vs_fp64": max([e for e, b in errs] or [0.0]),
+        "accuracy": {"f32": max([e for e, b in errs if not b] or [0.0]),
+                     "bf16": max([e for e, b in errs if b] or [0.0]), "requests_checked": len(errs)}}))
 
 
 if __name__ == "__main__":

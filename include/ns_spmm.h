@@ -149,7 +149,7 @@ ns_status_t ns_plan_stats(ns_plan_t p, ns_plan_stats_t* st);
 /* Copy one named plan array to host memory (for bit-exact comparison with the CPU reference
  * partition).  Names: aic_rows win_rows win_dptr dwin dwin_absorb dtile_cols dtile_bits
  * dtile_voff dtile_vals res_rowptr res_col res_val rl_rows rl_start chunk_b chunk_k0 row_split
- * split_row split_np split_slot split_fc queue item_cost.  ns_plan_array_info gives the element
+ * split_row split_np split_slot split_base queue item_cost.  ns_plan_array_info gives the element
  * count and size; `bytes` must be at least count * esize.  Synchronous. */
 ns_status_t ns_plan_array_info(ns_plan_t p, const char* name, int64_t* count, int32_t* esize);
 ns_status_t ns_plan_export(ns_plan_t p, const char* name, void* host_dst, int64_t bytes);
@@ -301,7 +301,8 @@ ns_status_t ns_serve_destroy(ns_server_t sv);
  *   caches it: make that first call before any stream capture.  Calls share the array and it
  *   keeps the last call's contents; each call clears its counters first.  Calls that overlap on
  *   the GPU (different streams or threads) race on the array and give wrong results.
- * Errors: NS_ERR_INVALID, NS_ERR_UNSUPPORTED (K, alignment), NS_ERR_TOO_LARGE, NS_ERR_CUDA. */
+ * Errors: NS_ERR_INVALID (also a CSR with n = 0 and nnz > 0), NS_ERR_UNSUPPORTED (K, alignment),
+ * NS_ERR_TOO_LARGE, NS_ERR_CUDA. */
 ns_status_t ns_spmm_csr_static(const ns_csr_t* A, const void* B, int64_t ldb, float* C, int64_t ldc,
                                int32_t K, ns_dtype_t b_dtype, ns_stream_t s);
 

@@ -6,8 +6,10 @@ product library: the two share no code, header or constant table.
 
 * :func:`spmm` -- the definition of SpMM (Section 5.1): ``C[i,:] = sum_p vals[p] * B[col[p],:]``
   in float64, ascending p, A and B widened to double first (BF16 B widened exactly).
-* :func:`plan` -- the CPU reference partition (Sections 5.2.2, 6.1 and 7, Eq. 1-5) that the
-  device planner must reproduce bit for bit.
+* :func:`plan` -- the CPU reference partition (Sections 5.2.2 and 6.1, Eq. 1-5): kept rows,
+  row windows, compacted dense tiles (bitmaps and packed values) and the residual CSR, which
+  the device planner must reproduce bit for bit.  How the execute kernel schedules the
+  partition (residual chunks, split rows, work-list order) is not part of it.
 * :func:`bf16_rne` -- round-to-nearest-even FP32 -> BF16 on the bit pattern (dense-tile values
   of the BF16 form).
 
@@ -33,19 +35,14 @@ _lib = None
 
 TAU_INF = 2147483647
 
-TUNE_FIELDS = ("TM", "TK", "tau_tile", "tau_row", "tau_col", "col_order", "chunk_nnz",
-               "absorb_cap", "group", "cost_tc", "cost_res", "reorder")
+TUNE_FIELDS = ("TM", "TK", "tau_tile", "tau_row", "tau_col", "col_order", "reorder")
 
-DEFAULT_TUNE = dict(TM=16, TK=16, tau_tile=TAU_INF, tau_row=0, tau_col=0, col_order=0,
-                    chunk_nnz=256, absorb_cap=256, group=4, cost_tc=1, cost_res=8, reorder=0)
+DEFAULT_TUNE = dict(TM=16, TK=16, tau_tile=TAU_INF, tau_row=0, tau_col=0, col_order=0, reorder=0)
 
-PLAN_ARRAYS = ("aic_rows", "win_rows", "win_dptr", "dwin", "dwin_absorb", "dtile_cols",
-               "dtile_bits", "dtile_voff", "dtile_vals", "res_rowptr", "res_col", "res_val",
-               "rl_rows", "rl_start", "chunk_b", "chunk_k0", "row_split", "split_row",
-               "split_np", "split_slot", "split_base", "queue", "item_cost")
+PLAN_ARRAYS = ("aic_rows", "win_rows", "win_dptr", "dtile_cols", "dtile_bits", "dtile_voff",
+               "dtile_vals", "res_rowptr", "res_col", "res_val")
 PLAN_SCALARS = ("m", "n", "nnz", "K", "b_bf16", "TM", "TK", "m_aic", "n_win", "n_dtiles",
-                "n_dwin", "n_dvals", "n_res", "n_rl", "T", "n_chunks", "n_split", "n_slots",
-                "n_items")
+                "n_dwin", "n_dvals", "n_res")
 
 
 class _Tune(ctypes.Structure):
@@ -152,11 +149,15 @@ class PlanError(ValueError):
 def plan(A: dict, K: int, *, b_bf16: bool = False, **tune) -> dict:
     """CPU reference partition of A.  Returns a dict of scalars and numpy arrays.
 
-    Keyword arguments override :data:`DEFAULT_TUNE`.  Raises :class:`PlanError` for an invalid
-    CSR (unsorted / duplicate / out-of-range column, non-monotone row pointers) or tune.
+    Keyword arguments override :data:`DEFAULT_TUNE`; any other key raises ``TypeError``.
+    Raises :class:`PlanError` for an invalid CSR (unsorted / duplicate / out-of-range column,
+    non-monotone row pointers) or tune.
     """
     lib = _load()
     t = dict(DEFAULT_TUNE)
+    unknown = set(tune) - set(DEFAULT_TUNE)
+    if unknown:
+        raise TypeError(f"not a partition parameter: {sorted(unknown)}")
     t.update(tune)
     tu = _Tune(*[int(t[f]) for f in TUNE_FIELDS])
     rowptr = np.ascontiguousarray(A["rowptr"], dtype=np.int32)
@@ -184,8 +185,6 @@ def plan(A: dict, K: int, *, b_bf16: bool = False, **tune) -> dict:
                 dt = np.uint32
             elif name == "res_val":
                 dt = np.float32
-            elif name == "item_cost":
-                dt = np.int64
             else:
                 dt = np.int32
             n_el = int(cnt.value)

@@ -1,9 +1,9 @@
 """Pure-Python brute-force partition for tiny matrices -- TEST INFRASTRUCTURE ONLY.
 
 An independent restatement of the reference partition (row/column extraction with the
-Len rule of Eq. 4-5, row windows and column compaction of Section 6.1, density binning
-with the integer tile threshold, the residual and its balanced chunks, Section 7), written
-with Python sets, dicts and a dense pattern instead of the C oracle's sorted arrays.  It pins
+Len rule of Eq. 4-5, Section 6.1 local reordering, row windows and column compaction, density
+binning with the integer tile threshold, and the residual of Section 5.2.2), written with
+Python sets, dicts and a dense pattern instead of the C oracle's sorted arrays.  It pins
 :func:`oracle.plan`: both must produce identical arrays on every tiny input.  O(m*n) memory;
 keep m, n <= a few hundred.
 """
@@ -108,84 +108,19 @@ def plan(A: dict, K: int, *, b_bf16: bool = False, **tune) -> dict:
     for i in range(m):
         res_rowptr.append(res_rowptr[-1] + len(res[i]))
 
-    owner = {}          # row -> (dense item index, absorbs)
-    dwin, dwin_absorb, dcost = [], [], []
-    for w, wr in enumerate(windows):
-        ntd = win_dptr[w + 1] - win_dptr[w]
-        if ntd == 0:
-            continue
-        rows_w = [i for i in wr if i >= 0]
-        res_w = sum(len(res[i]) for i in rows_w)
-        absorb = res_w <= t["absorb_cap"]
-        for i in rows_w:
-            owner[i] = (len(dwin), absorb)
-        dwin.append(w)
-        dwin_absorb.append(1 if absorb else 0)
-        dcost.append(ntd * TM * TK * t["cost_tc"] + ((res_w if absorb else 0) + len(rows_w)) * t["cost_res"])
-
-    rl = [i for i in range(m) if i not in owner or (not owner[i][1] and len(res[i]) > 0)]
-    starts = [0]
-    for i in rl:
-        starts.append(starts[-1] + len(res[i]) + 1)
-    T = starts[-1]
-    W = t["chunk_nnz"]
-    nc = -(-T // W) if T else 0
-    # merge item x belongs to RL row k when starts[k] <= x < starts[k+1]
-    item_row = []
-    for k, i in enumerate(rl):
-        item_row += [k] * (len(res[i]) + 1)
-    bounds = [0]
-    for c in range(1, nc):
-        k = item_row[c * W]
-        bounds.append(starts[k] if 2 * (len(res[rl[k]]) + 1) <= W else c * W)
-    if nc:
-        bounds.append(T)
-    chunk_of_item = []
-    for c in range(nc):
-        chunk_of_item += [c] * (bounds[c + 1] - bounds[c])
-    chunk_k0 = [item_row[bounds[c]] for c in range(nc)]
-
-    pieces = {i: 1 for i in owner}
-    first_chunk = {}
-    for k, i in enumerate(rl):
-        chunks = set(chunk_of_item[starts[k]:starts[k + 1]])
-        pieces[i] = pieces.get(i, 0) + len(chunks)
-        first_chunk[i] = min(chunks)
-    split = [i for i in range(m) if pieces.get(i, 0) >= 2]
-    row_split = [-1] * m
-    split_np, split_slot, split_base = [], [], []
-    slot = 0
-    for s, i in enumerate(split):
-        row_split[i] = s
-        split_np.append(pieces[i])
-        split_slot.append(slot)
-        split_base.append(first_chunk[i] - (1 if i in owner else 0))
-        slot += pieces[i]
-
-    G = t["group"]
-    nq = -(-nc // G) if nc else 0
-    costs = list(dcost) + [(bounds[min(q * G + G, nc)] - bounds[q * G]) * t["cost_res"]
-                           for q in range(nq)]
-    bucket = [c.bit_length() - 1 if c >= 1 else 0 for c in costs]
-    queue = sorted(range(len(costs)), key=lambda it: (-bucket[it], it))
-
     if b_bf16:
         dvals_arr = _bf16_library(np.asarray(dvals, dtype=np.float32)) if dvals else np.zeros(0, np.uint16)
     else:
         dvals_arr = np.asarray(dvals, dtype=np.float32)
     i32 = lambda x: np.asarray(x, dtype=np.int32)
     return dict(
-        m=m, n=n, m_aic=len(aic), n_win=n_win, n_dtiles=len(tiles), n_dwin=len(dwin),
-        n_dvals=voff[-1], n_res=res_rowptr[-1], n_rl=len(rl), T=T, n_chunks=nc,
-        n_split=len(split), n_slots=slot, n_items=len(costs),
+        m=m, n=n, m_aic=len(aic), n_win=n_win, n_dtiles=len(tiles),
+        n_dwin=sum(1 for w in range(n_win) if win_dptr[w + 1] > win_dptr[w]),
+        n_dvals=voff[-1], n_res=res_rowptr[-1],
         aic_rows=i32(aic), win_rows=i32([i for wr in windows for i in wr]),
-        win_dptr=i32(win_dptr), dwin=i32(dwin), dwin_absorb=i32(dwin_absorb),
+        win_dptr=i32(win_dptr),
         dtile_cols=i32(dtile_cols), dtile_bits=np.asarray(dtile_bits, dtype=np.uint32),
         dtile_voff=i32(voff), dtile_vals=dvals_arr,
         res_rowptr=i32(res_rowptr), res_col=i32([j for r in res for j, _ in r]),
         res_val=np.asarray([x for r in res for _, x in r], dtype=np.float32),
-        rl_rows=i32(rl), rl_start=i32(starts), chunk_b=i32(bounds if nc else [0]),
-        chunk_k0=i32(chunk_k0), row_split=i32(row_split), split_row=i32(split),
-        split_np=i32(split_np), split_slot=i32(split_slot), split_base=i32(split_base),
-        queue=i32(queue), item_cost=np.asarray(costs, dtype=np.int64),
     )

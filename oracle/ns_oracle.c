@@ -13,12 +13,14 @@
  *     double precision with A's FP32 values and B's values (FP32, or BF16 widened exactly)
  *     first widened to double, accumulated in ascending p.
  *
- *  2. orc_plan_build -- the CPU reference partition.  It takes the method's planning steps in
- *     the paper's order (Section 5.2.2 row/column extraction with the Len rule of Eq. 4-5,
- *     Section 6.1 row windows and column compaction, the tile density rule derived from the
- *     cost model of Eq. 1-3, Section 7 row-window list balancing) with the integer readings
- *     written down in the project design notes.  The device planner must reproduce every array
- *     it emits bit for bit.
+ *  2. orc_plan_build -- the CPU reference partition of A.  It takes the method's planning steps
+ *     in the paper's order (Section 5.2.2 row/column extraction with the Len rule of Eq. 4-5,
+ *     Section 6.1 local reordering, row windows and column compaction, the tile density rule
+ *     derived from the cost model of Eq. 1-3, the residual of Section 5.2.2) with the integer
+ *     readings written down in the project design notes.  The device planner must reproduce
+ *     every array it emits bit for bit.  How the execute kernel then schedules that partition
+ *     (residual chunks, split rows, the work-list order) is not the paper's partition and is not
+ *     restated here: the tests check it by invariants and by the product.
  *
  * Everything is deliberately simple: loops, qsort, binary search.  No blocking, no fusion.
  */
@@ -98,41 +100,22 @@ typedef struct {
     int32_t tau_row;     /* row goes to the residual iff Len(row) <= tau_row (Eq. 4-5)           */
     int32_t tau_col;     /* column (inside the window rows) to residual iff count <= tau_col      */
     int32_t col_order;   /* 0: count descending then column ascending; 1: column ascending       */
-    int32_t chunk_nnz;   /* W: merge items (residual nnz + row ends) per residual chunk           */
-    int32_t absorb_cap;  /* a dense window keeps its rows' residual if their nnz <= absorb_cap     */
-    int32_t group;       /* residual chunks per residual work item                               */
-    int32_t cost_tc;     /* Eq. 1 cost weight of one tile element                                */
-    int32_t cost_res;    /* Eq. 1 cost weight of one residual nonzero                            */
     int32_t reorder;     /* Section 6.1 local reordering: windows per cluster (0: off)            */
 } orc_tune;
 
 typedef struct {
     int64_t m, n, nnz, K, b_bf16, TM, TK;
-    int64_t m_aic, n_win, n_dtiles, n_dwin, n_dvals, n_res, n_rl, T, n_chunks, n_split, n_slots,
-        n_items;
-    int32_t* aic_rows;
-    int32_t* win_rows;
-    int32_t* win_dptr;
-    int32_t* dwin;
-    int32_t* dwin_absorb;
-    int32_t* dtile_cols;
-    uint32_t* dtile_bits;
-    int32_t* dtile_voff;
-    void* dtile_vals;
-    int32_t* res_rowptr;
+    int64_t m_aic, n_win, n_dtiles, n_dwin, n_dvals, n_res;
+    int32_t* aic_rows;   /* rows kept for windows, in window order                               */
+    int32_t* win_rows;   /* n_win * TM rows, the last window padded with -1                      */
+    int32_t* win_dptr;   /* dense tiles of window w: [win_dptr[w], win_dptr[w + 1])              */
+    int32_t* dtile_cols; /* TK column ids per dense tile (-1 past the window's last column)      */
+    uint32_t* dtile_bits;/* TM x TK row-major bitmap per dense tile                              */
+    int32_t* dtile_voff; /* first packed value of each dense tile (padded to 8 per tile)         */
+    void* dtile_vals;    /* packed values in bitmap order (FP32, or BF16 rounded to nearest even) */
+    int32_t* res_rowptr; /* residual CSR over the original m rows                                */
     int32_t* res_col;
     float* res_val;
-    int32_t* rl_rows;
-    int32_t* rl_start;
-    int32_t* chunk_b;
-    int32_t* chunk_k0;
-    int32_t* row_split;
-    int32_t* split_row;
-    int32_t* split_np;
-    int32_t* split_slot;
-    int32_t* split_base;
-    int32_t* queue;
-    int64_t* item_cost;
 } orc_plan;
 
 typedef struct {
@@ -153,18 +136,6 @@ static int cmp_ucol_count_desc(const void* a, const void* b)
     return (x->col > y->col) - (x->col < y->col);
 }
 
-/* index of the largest k in [0, count) with arr[k] <= key (arr non-decreasing, arr[0] <= key) */
-static int64_t upper_minus_one(const int32_t* arr, int64_t count, int64_t key)
-{
-    int64_t lo = 0, hi = count; /* answer in [lo, hi) */
-    while (hi - lo > 1) {
-        int64_t mid = lo + (hi - lo) / 2;
-        if ((int64_t)arr[mid] <= key) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
 /* position of column j inside the sorted row segment colidx[b, e); -1 if absent */
 static int64_t find_in_row(const int32_t* colidx, int64_t b, int64_t e, int32_t j)
 {
@@ -180,11 +151,9 @@ static int64_t find_in_row(const int32_t* colidx, int64_t b, int64_t e, int32_t 
 void orc_plan_free(orc_plan* p)
 {
     if (!p) return;
-    free(p->aic_rows); free(p->win_rows); free(p->win_dptr); free(p->dwin); free(p->dwin_absorb);
+    free(p->aic_rows); free(p->win_rows); free(p->win_dptr);
     free(p->dtile_cols); free(p->dtile_bits); free(p->dtile_voff); free(p->dtile_vals);
-    free(p->res_rowptr); free(p->res_col); free(p->res_val); free(p->rl_rows); free(p->rl_start);
-    free(p->chunk_b); free(p->chunk_k0); free(p->row_split); free(p->split_row);
-    free(p->split_np); free(p->split_slot); free(p->split_base); free(p->queue); free(p->item_cost);
+    free(p->res_rowptr); free(p->res_col); free(p->res_val);
     free(p);
 }
 
@@ -219,7 +188,7 @@ int orc_plan_build(int32_t m, int32_t n, const int32_t* rowptr, const int32_t* c
     }
     const int32_t TM = tu->TM, TK = tu->TK;
     if (!(TM == 16 || TM == 32 || TM == 64) || !(TK == 16 || TK == 32)) return 1;
-    if (tu->chunk_nnz < 2 || tu->group < 1 || tu->cost_tc < 0 || tu->cost_res < 0) return 1;
+    if (tu->reorder < 0) return 1;
     const int64_t nnz = rowptr[m];
     const int32_t BW = TM * TK / 32; /* bitmap words per tile */
 
@@ -466,141 +435,13 @@ int orc_plan_build(int32_t m, int32_t n, const int32_t* rowptr, const int32_t* c
                 if (!is_dense_elem[p]) { P->res_col[z] = colidx[p]; P->res_val[z] = vals[p]; ++z; }
     }
 
-    /* ---- row ownership: dense windows own their rows; a dense window keeps (absorbs) its
-     *      rows' residual nonzeros when there are at most absorb_cap of them ---- */
-    int64_t n_dwin = 0;
-    for (int64_t w = 0; w < n_win; ++w) n_dwin += P->win_dptr[w + 1] > P->win_dptr[w];
-    P->n_dwin = n_dwin;
-    P->dwin = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_dwin > 0 ? n_dwin : 1));
-    P->dwin_absorb = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_dwin > 0 ? n_dwin : 1));
-    int8_t* row_state = (int8_t*)calloc((size_t)(m > 0 ? m : 1), 1); /* 0 free, 1 dense+absorb, 2 dense */
-    int64_t* dcost = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_dwin > 0 ? n_dwin : 1));
+    /* ---- windows with at least one dense tile (the matrix engine's row-window list) ---- */
     {
-        int64_t d = 0;
-        for (int64_t w = 0; w < n_win; ++w) {
-            if (P->win_dptr[w + 1] == P->win_dptr[w]) continue;
-            int64_t res_w = 0, nvalid = 0;
-            for (int32_t r = 0; r < TM; ++r) {
-                int32_t i = P->win_rows[w * TM + r];
-                if (i < 0) continue;
-                ++nvalid;
-                res_w += P->res_rowptr[i + 1] - P->res_rowptr[i];
-            }
-            int absorb = res_w <= tu->absorb_cap;
-            P->dwin[d] = (int32_t)w;
-            P->dwin_absorb[d] = absorb;
-            for (int32_t r = 0; r < TM; ++r) {
-                int32_t i = P->win_rows[w * TM + r];
-                if (i >= 0) row_state[i] = absorb ? 1 : 2;
-            }
-            int64_t ntd = P->win_dptr[w + 1] - P->win_dptr[w];
-            dcost[d] = ntd * TM * TK * (int64_t)tu->cost_tc + ((absorb ? res_w : 0) + nvalid) * (int64_t)tu->cost_res;
-            ++d;
-        }
+        int64_t n_dwin = 0;
+        for (int64_t w = 0; w < n_win; ++w) n_dwin += P->win_dptr[w + 1] > P->win_dptr[w];
+        P->n_dwin = n_dwin;
     }
 
-    /* ---- residual row list and merge-path chunks (Section 7, balanced lists) ---- */
-    int64_t n_rl = 0;
-    for (int32_t i = 0; i < m; ++i) {
-        int32_t rl = P->res_rowptr[i + 1] - P->res_rowptr[i];
-        if (row_state[i] == 0 || (row_state[i] == 2 && rl > 0)) ++n_rl;
-    }
-    P->n_rl = n_rl;
-    P->rl_rows = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_rl > 0 ? n_rl : 1));
-    P->rl_start = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_rl + 1));
-    {
-        int64_t k = 0;
-        P->rl_start[0] = 0;
-        for (int32_t i = 0; i < m; ++i) {
-            int32_t rl = P->res_rowptr[i + 1] - P->res_rowptr[i];
-            if (row_state[i] == 0 || (row_state[i] == 2 && rl > 0)) {
-                P->rl_rows[k] = i;
-                P->rl_start[k + 1] = P->rl_start[k] + rl + 1;
-                ++k;
-            }
-        }
-    }
-    const int64_t T = P->rl_start[n_rl];
-    const int64_t W = tu->chunk_nnz;
-    P->T = T;
-    const int64_t nc = T > 0 ? (T + W - 1) / W : 0;
-    P->n_chunks = nc;
-    P->chunk_b = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nc + 1));
-    P->chunk_k0 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nc > 0 ? nc : 1));
-    P->chunk_b[0] = 0;
-    for (int64_t c = 1; c < nc; ++c) {
-        int64_t dgn = c * W;
-        int64_t k = upper_minus_one(P->rl_start, n_rl, dgn);
-        int64_t rlen = P->res_rowptr[P->rl_rows[k] + 1] - P->res_rowptr[P->rl_rows[k]];
-        P->chunk_b[c] = (int32_t)((2 * (rlen + 1) <= W) ? P->rl_start[k] : dgn);
-    }
-    if (nc > 0) P->chunk_b[nc] = (int32_t)T;
-    for (int64_t c = 0; c < nc; ++c)
-        P->chunk_k0[c] = (int32_t)upper_minus_one(P->rl_start, n_rl, P->chunk_b[c]);
-
-    /* ---- pieces per row; rows with two or more pieces are split rows ---- */
-    int32_t* npieces = (int32_t*)calloc((size_t)(m > 0 ? m : 1), sizeof(int32_t));
-    int32_t* firstc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
-    for (int32_t i = 0; i < m; ++i) { npieces[i] = row_state[i] ? 1 : 0; firstc[i] = -1; }
-    for (int64_t k = 0; k < n_rl; ++k) {
-        int32_t i = P->rl_rows[k];
-        int64_t fc = upper_minus_one(P->chunk_b, nc, P->rl_start[k]);
-        int64_t lc = upper_minus_one(P->chunk_b, nc, (int64_t)P->rl_start[k + 1] - 1);
-        npieces[i] += (int32_t)(lc - fc + 1);
-        firstc[i] = (int32_t)fc;
-    }
-    int64_t n_split = 0;
-    for (int32_t i = 0; i < m; ++i) n_split += npieces[i] >= 2;
-    P->n_split = n_split;
-    P->row_split = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
-    P->split_row = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_split > 0 ? n_split : 1));
-    P->split_np = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_split > 0 ? n_split : 1));
-    P->split_slot = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_split > 0 ? n_split : 1));
-    P->split_base = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_split > 0 ? n_split : 1));
-    {
-        int64_t s = 0, slot = 0;
-        for (int32_t i = 0; i < m; ++i) {
-            if (npieces[i] >= 2) {
-                P->row_split[i] = (int32_t)s;
-                P->split_row[s] = i;
-                P->split_np[s] = npieces[i];
-                P->split_slot[s] = (int32_t)slot;
-                /* chunk c delivers piece c - split_base; a dense window, if any, piece 0 */
-                P->split_base[s] = firstc[i] - (row_state[i] ? 1 : 0);
-                slot += npieces[i];
-                ++s;
-            } else {
-                P->row_split[i] = -1;
-            }
-        }
-        P->n_slots = slot;
-    }
-
-    /* ---- work items and their order: cost classes (floor log2 of the Eq. 1 cost) from
-     *      heaviest to lightest, then item id; dense items come before residual items ---- */
-    const int64_t G = tu->group;
-    const int64_t nq = (nc + G - 1) / G;
-    const int64_t n_items = n_dwin + nq;
-    P->n_items = n_items;
-    P->queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_items > 0 ? n_items : 1));
-    P->item_cost = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_items > 0 ? n_items : 1));
-    for (int64_t d = 0; d < n_dwin; ++d) P->item_cost[d] = dcost[d];
-    for (int64_t q = 0; q < nq; ++q) {
-        int64_t c1 = (q + 1) * G < nc ? (q + 1) * G : nc;
-        P->item_cost[n_dwin + q] = ((int64_t)P->chunk_b[c1] - P->chunk_b[q * G]) * tu->cost_res;
-    }
-    {
-        int64_t k = 0;
-        for (int bucket = 62; bucket >= 0; --bucket)
-            for (int64_t it = 0; it < n_items; ++it) {
-                int64_t c = P->item_cost[it];
-                int b = 0;
-                while (b < 62 && (c >> (b + 1)) > 0) ++b; /* floor(log2(c)), 0 for c <= 1 */
-                if (b == bucket) P->queue[k++] = (int32_t)it;
-            }
-    }
-
-    free(npieces); free(firstc); free(row_state); free(dcost);
     free(len); free(is_dense_elem); free(aic_col);
     free(dcols); free(dbits); free(dtnnz); free(wcols); free(uc); free(uasc); free(upos); free(tile_rank);
     *out = P;
@@ -621,7 +462,7 @@ int64_t orc_plan_scalar(const orc_plan* P, const char* name)
 {
 #define S(x) if (!strcmp(name, #x)) return P->x;
     S(m) S(n) S(nnz) S(K) S(b_bf16) S(TM) S(TK) S(m_aic) S(n_win) S(n_dtiles) S(n_dwin) S(n_dvals)
-    S(n_res) S(n_rl) S(T) S(n_chunks) S(n_split) S(n_slots) S(n_items)
+    S(n_res)
 #undef S
     return -1;
 }
@@ -635,8 +476,6 @@ int orc_plan_array(const orc_plan* P, const char* name, const void** ptr, int64_
     A(aic_rows, P->m_aic, 4)
     A(win_rows, P->n_win * TM, 4)
     A(win_dptr, P->n_win + 1, 4)
-    A(dwin, P->n_dwin, 4)
-    A(dwin_absorb, P->n_dwin, 4)
     A(dtile_cols, P->n_dtiles * TK, 4)
     A(dtile_bits, P->n_dtiles * BW, 4)
     A(dtile_voff, P->n_dtiles + 1, 4)
@@ -644,17 +483,6 @@ int orc_plan_array(const orc_plan* P, const char* name, const void** ptr, int64_
     A(res_rowptr, P->m + 1, 4)
     A(res_col, P->n_res, 4)
     A(res_val, P->n_res, 4)
-    A(rl_rows, P->n_rl, 4)
-    A(rl_start, P->n_rl + 1, 4)
-    A(chunk_b, P->n_chunks + 1, 4)
-    A(chunk_k0, P->n_chunks, 4)
-    A(row_split, P->m, 4)
-    A(split_row, P->n_split, 4)
-    A(split_np, P->n_split, 4)
-    A(split_slot, P->n_split, 4)
-    A(split_base, P->n_split, 4)
-    A(queue, P->n_items, 4)
-    A(item_cost, P->n_items, 8)
 #undef A
     return 1;
 }

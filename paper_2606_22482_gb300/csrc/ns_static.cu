@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(128) k_spmm_static(StaticArgs a)
                 if (lane < cntb) {
                     mc = __ldg(a.colidx + zb + lane);
                     mv = __ldg(a.vals + zb + lane);
-                    if ((unsigned)mc >= (unsigned)a.n) mc = 0, mv = 0.f;  // never gather outside B
+                    if ((unsigned)mc >= (unsigned)a.n) mc = -1, mv = 0.f;  // never gather outside B
                 }
                 for (int j0 = 0; j0 < cntb; j0 += G) {
                     const int j = j0 + g;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(128) k_spmm_static(StaticArgs a)
 #pragma unroll
                     for (int q = 0; q < VPL; ++q) {
                         const int v = li + L * q;
-                        if (j < cntb && v < nv) {
+                        if (j < cntb && col >= 0 && v < nv) {  // an invalid column gathers nothing
                             float4 b = st_ldb<BF16>(a.B, (int64_t)col * a.ldb + 4 * v);
                             acc[q].x = fmaf(val, b.x, acc[q].x);
                             acc[q].y = fmaf(val, b.y, acc[q].y);
@@ -217,6 +217,10 @@ extern "C" ns_status_t ns_spmm_csr_static(const ns_csr_t* A, const void* B, int6
     }
     if (!A->rowptr || (A->nnz > 0 && (!A->colidx || !A->vals)) || (A->n > 0 && !B) || (A->m > 0 && !C)) {
         set_error("NULL array");
+        return NS_ERR_INVALID;
+    }
+    if (A->nnz > 0 && A->n == 0) {  // no column index can be valid, and B has no rows
+        set_error("CSR with n = 0 columns cannot hold %lld nonzeros", (long long)A->nnz);
         return NS_ERR_INVALID;
     }
     if (K < 8 || K > 1024 || K % 8) {

@@ -1,7 +1,5 @@
-"""Helpers shared by the GPU tests (device transfer, plan comparison)."""
+"""Helpers shared by the GPU tests (device transfer, tunes, plan comparison)."""
 import numpy as np
-
-import oracle
 
 
 def to_dev(A, dev):
@@ -17,25 +15,4 @@ def tune_from(ns, **kw):
     return t
 
 
-def oracle_tune(t):
-    d = t.as_dict()
-    d.pop("l2_hints")
-    d.pop("TN")
-    return d
-
-
-def compare_plan(plan, ref):
-    """Every plan array bit-exact against the CPU reference partition."""
-    st = plan.stats()
-    for k in oracle.PLAN_SCALARS:
-        assert st[k] == ref[k], f"scalar {k}: device {st[k]} vs reference {ref[k]}"
-    for name in oracle.PLAN_ARRAYS:
-        got = plan.export(name)
-        exp = np.asarray(ref[name])
-        if name in ("win_dptr",) and ref["n_win"] == 0:
-            continue
-        assert got.dtype == exp.dtype, (name, got.dtype, exp.dtype)
-        assert got.shape == exp.shape, (name, got.shape, exp.shape)
-        if not np.array_equal(got.view(np.uint8), exp.view(np.uint8)):
-            bad = np.nonzero(got != exp)[0][:10]
-            raise AssertionError(f"plan array {name} differs at {bad}: {got[bad]} vs {exp[bad]}")
+from plan_checks import compare_plan, oracle_tune  # noqa: E402,F401

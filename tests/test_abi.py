@@ -70,3 +70,32 @@ def test_argument_errors_without_a_device(ns):
     h = ctypes.c_void_p()
     assert lib.ns_spmm_plan(ctypes.byref(c), 32, ns.NS_F32, ctypes.byref(t), None, ctypes.byref(h)) == 1
     assert b"tune" in lib.ns_last_error()
+
+
+def test_static_rejects_zero_columns_before_any_device_call(ns):
+    # a CSR with nonzeros but no columns cannot be valid, and B has no row to gather: the
+    # allocation-free entry point refuses it on the host instead of launching
+    import ctypes
+    lib = ns.lib
+    rp = (ctypes.c_int32 * 5)(0, 1, 2, 3, 3)
+    ci = (ctypes.c_int32 * 3)(0, 0, 0)
+    vv = (ctypes.c_float * 3)(1.0, 1.0, 1.0)
+    cbuf = (ctypes.c_float * 64)()
+    c = ns._abi.Csr(4, 0, 3, ctypes.cast(rp, ctypes.c_void_p), ctypes.cast(ci, ctypes.c_void_p),
+                    ctypes.cast(vv, ctypes.c_void_p), 1)
+    rc = lib.ns_spmm_csr_static(ctypes.byref(c), None, 8, ctypes.cast(cbuf, ctypes.c_void_p), 8, 8,
+                                ns.NS_F32, None)
+    assert rc == 1                                                          # NS_ERR_INVALID
+    assert b"n = 0" in lib.ns_last_error()
+
+
+def test_header_export_names_match_library_and_binding(ns):
+    # the names ns_plan_export accepts, as listed in the header, are the ones the library's
+    # lookup table holds and the ones the binding knows
+    src = open(os.path.join(ROOT, "include", "ns_spmm.h")).read()
+    m = re.search(r"Names:(.*?)\.\s+ns_plan_array_info", src, re.S)
+    listed = m.group(1).replace("*", " ").split()
+    api = open(os.path.join(ROOT, "paper_2606_22482_gb300", "csrc", "ns_api.cu")).read()
+    table = re.findall(r"^\s*A\((\w+),", api, re.M)
+    assert listed == table
+    assert tuple(listed) == tuple(ns.PLAN_ARRAYS)

@@ -15,6 +15,15 @@ def test_reference_arm_json_line():
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference"
+    # the driver divides the two arms only when metric, unit and direction are identical
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("_bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert line["metric"] == bench.METRIC
+    assert "whole matrix" in line["cpu_baseline"]["sample"]
+    st = line["cpu_baseline"]["single_thread"]
+    assert st["cores"] == 1 and st["value"] > 0 and line["cpu_baseline"]["cpu_model"]
     assert line["unit"] == "GFLOP/s" and line["value"] > 0 and line["higher_is_better"] is True
     assert line["steps"] == 1 and line["warmup"] == 0 and line["n_gpus"] == 1
     assert line["config"]["workload"].startswith("powerlaw-rmat-2^20")

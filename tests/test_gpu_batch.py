@@ -97,3 +97,31 @@ def test_autotune_gives_valid_fast_tune(which):
         p.execute(torch.from_numpy(B).to(DEV), C)
         torch.cuda.synchronize()
     assert oracle.rel_frobenius(C.cpu().numpy(), oracle.spmm(A, B)) <= 1e-5
+
+
+@pytest.mark.slow
+def test_batched_config_at_size():
+    # the batched workload at its full size: 512 uneven graphs (node counts log-uniform in
+    # [1e3, 5e4], mean degree 8-32, about 128 M nonzeros), K = 64, one persistent launch replayed
+    # from a CUDA graph; every graph compared in full with the FP64 oracle
+    import os
+    from parity import check_result
+    threads = max(1, min(16, len(os.sched_getaffinity(0))))
+    graphs, Bs = synth.config_batched(0)
+    K = 64
+    assert len(graphs) == 512
+    Ad = [to_dev(g, DEV) for g in graphs]
+    Bd = [torch.from_numpy(b).to(DEV) for b in Bs]
+    Cd = [torch.full((g["m"], K), float("nan"), device=DEV) for g in graphs]
+    bt = ns.Batch(Ad, [K] * len(graphs), ns.NS_F32, tune_from(ns, chunk_nnz=512, absorb_cap=512))
+    launches = ns.launch_count()
+    for _ in range(2):                                  # capture, then one replay
+        bt.execute(Bd, Cd)
+    torch.cuda.synchronize()
+    assert ns.launch_count() - launches == 2
+    worst = 0.0
+    for g, b, c in zip(graphs, Bs, Cd):
+        rep = check_result(c.cpu().numpy(), g, b, tol=1e-5, threads=threads)
+        worst = max(worst, rep["rel_frobenius"])
+    print(f"\n[parity] batched 512 graphs, {sum(g.nnz for g in graphs)} nnz: max rel. Frobenius {worst:.3e}")
+    bt.close()

@@ -1,5 +1,6 @@
-"""Parity of the CUDA path against the FP64 oracle (GPU): plans bit-exact with the CPU
-reference partition, results within the FP32 / BF16 tolerances, exact cases exact."""
+"""Parity of the CUDA path against the FP64 oracle (GPU): the plan's partition bit-exact with the
+CPU reference partition and its execute bookkeeping valid, results within the FP32 / BF16
+tolerances, exact cases exact."""
 import numpy as np
 import pytest
 
@@ -33,7 +34,7 @@ def run(A, B, dtype=ns.NS_F32, tune=None, check_plan=True, C=None):
     Ct = torch.full((A["m"], K), float("nan"), device=DEV) if C is None else C
     with ns.spmm_plan(At, K, dtype, tune) as p:
         if check_plan:
-            compare_plan(p, oracle.plan(A, K, b_bf16=dtype == ns.NS_BF16, **oracle_tune(tune)))
+            compare_plan(p, oracle.plan(A, K, b_bf16=dtype == ns.NS_BF16, **oracle_tune(tune)), A, tune)
         p.execute(Bt, Ct)
         torch.cuda.synchronize()
         c1 = Ct.cpu().numpy()
@@ -153,7 +154,7 @@ def test_host_csr_plan_equals_device_plan():
     A = synth.rmat_csr(11, 20000, seed=9)
     t = tune_from(ns, chunk_nnz=32)
     with ns.spmm_plan(A, 32, ns.NS_F32, t, device=False) as ph:
-        compare_plan(ph, oracle.plan(A, 32, **oracle_tune(t)))
+        compare_plan(ph, oracle.plan(A, 32, **oracle_tune(t)), A, t)
 
 
 def test_spmm_host_entry():
@@ -184,3 +185,53 @@ def test_column_slices(K, TN):
     assert np.array_equal(c_sl, c_sl2)
     assert oracle.rel_frobenius(c_sl, ref) <= 1e-6
     assert oracle.rel_frobenius(c_full, ref) <= 1e-6
+
+
+@pytest.mark.parametrize("tau", [ns.NS_TAU_INF, 8])
+@pytest.mark.parametrize("dtype", [ns.NS_F32, ns.NS_BF16])
+def test_hot_rows_l2_policy(tau, dtype):
+    # Section 6.2.1 hot-B staging (l2_hints = 2): the planner marks the most gathered B rows and
+    # the gathers pick their L2 policy from that map; the product must not change
+    A = synth.rmat_csr(13, 120000, seed=17)
+    B = synth.dense_b(A["n"], 64, seed=18)
+    c, ref = run(A, B, dtype, tune=tune_from(ns, tau_tile=tau, TM=16, l2_hints=2))
+    assert oracle.rel_frobenius(c, ref) <= TOL[dtype]
+    c1, _ = run(A, B, dtype, tune=tune_from(ns, tau_tile=tau, TM=16, l2_hints=1), check_plan=False)
+    assert oracle.rel_frobenius(c1, ref) <= TOL[dtype]
+
+
+def test_bookkeeping_checker_bites():
+    # the invariant checker of the execute bookkeeping accepts the device plan and rejects
+    # planted mistakes in each of its arrays
+    from plan_checks import check_bookkeeping, exports
+    A = synth.random_csr(400, 500, 0.03, seed=5, hub_rows=4, empty_rows=0.2)
+    t = tune_from(ns, tau_tile=6, TM=16, TK=16, chunk_nnz=16, absorb_cap=8)
+    part = oracle.plan(A, 32, **oracle_tune(t))
+    with ns.spmm_plan(to_dev(A, DEV), 32, ns.NS_F32, t) as p:
+        st, ex = p.stats(), exports(p)
+    td = t.as_dict()
+    check_bookkeeping(A, part, st, ex, td)
+    assert st["n_split"] > 0 and st["n_dwin"] > 0 and st["n_chunks"] > 2
+
+    def bump(name, k, d=1):
+        def f(e):
+            e[name] = e[name].copy()
+            e[name][k] += d
+        return f
+
+    def swap_queue(e):
+        e["queue"] = e["queue"].copy()
+        e["queue"][[0, -1]] = e["queue"][[-1, 0]]
+
+    def drop_rl(e):
+        e["rl_rows"] = e["rl_rows"][:-1].copy()
+
+    mutations = [bump("chunk_b", 1), bump("chunk_k0", 1), bump("split_base", 0), bump("split_slot", 1),
+                 bump("split_np", 0), bump("row_split", int(np.argmax(ex["row_split"] < 0)), 1),
+                 bump("dwin_absorb", 0), bump("rl_start", 2), bump("item_cost", 0, 1 << 20),
+                 swap_queue, drop_rl]
+    for mutate in mutations:
+        bad = {k: v for k, v in ex.items()}
+        mutate(bad)
+        with pytest.raises(AssertionError):
+            check_bookkeeping(A, part, st, bad, td)

@@ -2,7 +2,7 @@
 
 * the C planner equals the pure-Python brute-force planner on tiny inputs, for many tunes;
 * partition invariants hold (every nonzero exactly once, reconstruction, thresholds, window
-  coverage, chunk balance, split-row bookkeeping, queue order);
+  coverage, the row extraction rule);
 * the product evaluated from the plan equals the SpMM definition;
 * the paper's closed forms (Eq. 1-3, 6, 8 and the tile-shape worked numbers).
 """
@@ -40,14 +40,14 @@ TINY_TUNES = [
     dict(tau_tile=6, TM=32, TK=16, col_order=1),
     dict(tau_tile=2, TM=16, TK=32, tau_row=2),
     dict(tau_tile=2, TM=16, TK=16, tau_col=1),
-    dict(tau_tile=4, TM=64, TK=16, chunk_nnz=8, absorb_cap=3, group=2),
-    dict(tau_tile=5, TM=16, TK=16, chunk_nnz=5, absorb_cap=0, group=3, cost_tc=3, cost_res=1),
-    dict(tau_tile=INF, chunk_nnz=3, group=1),
-    dict(tau_tile=6, TM=16, TK=16, chunk_nnz=4, absorb_cap=0, group=2),
-    dict(tau_tile=12, TM=16, TK=16, chunk_nnz=6, absorb_cap=2, tau_row=1, col_order=1),
+    dict(tau_tile=4, TM=64, TK=16),
+    dict(tau_tile=5, TM=16, TK=16),
+    dict(tau_tile=6, TM=16, TK=16, tau_row=3),
+    dict(tau_tile=12, TM=16, TK=16, tau_row=1, col_order=1),
     dict(tau_tile=3, TM=16, TK=16, reorder=1),
     dict(tau_tile=2, TM=16, TK=16, reorder=3, tau_col=1),
     dict(tau_tile=5, TM=32, TK=16, reorder=2, tau_row=1),
+    dict(tau_tile=9, TM=32, TK=32, tau_col=2, col_order=1),
 ]
 
 
@@ -120,36 +120,14 @@ def _check_invariants(A, P):
                 assert got == oracle.bf16_rne(np.array([v[p]]))[0]
             else:
                 assert np.float32(got).view(np.uint32) == v[p].view(np.uint32)
-    # merge-path chunks: strictly increasing, balanced within [W/2, 3W/2] except the last
-    W = t["chunk_nnz"]
-    b = P["chunk_b"]
-    if P["n_chunks"]:
-        assert b[0] == 0 and b[-1] == P["T"]
-        sizes = np.diff(b)
-        assert np.all(sizes > 0)
-        assert np.all(sizes[:-1] * 2 >= W - 1) and np.all(sizes * 2 <= 3 * W)
-    # pieces: every row is owned by something; slots add up
-    assert P["n_slots"] == int(P["split_np"].sum())
-    if P["n_split"]:
-        assert np.all(P["split_np"] >= 2)
-        assert np.array_equal(P["split_slot"], np.concatenate([[0], np.cumsum(P["split_np"])[:-1]]))
-    rs = P["row_split"]
-    assert np.array_equal(np.nonzero(rs >= 0)[0], P["split_row"])
-    in_dense = set(wr[w * TM + r] for w in P["dwin"] for r in range(TM) if wr[w * TM + r] >= 0)
-    rl = set(P["rl_rows"].tolist())
-    assert in_dense | rl == set(range(m))
-    # short residual rows are never cut by a chunk boundary
-    for k, i in enumerate(P["rl_rows"]):
-        rlen = rrp[i + 1] - rrp[i]
-        if 2 * (rlen + 1) <= W and i not in in_dense:
-            assert rs[i] == -1
-    # queue: a permutation of the items, heaviest cost class first
-    q = P["queue"]
-    assert sorted(q.tolist()) == list(range(P["n_items"]))
-    cost = P["item_cost"]
-    buck = np.array([int(c).bit_length() - 1 if c >= 1 else 0 for c in cost])
-    if len(q):
-        assert np.all(np.diff(buck[q]) <= 0)
+    # the row-window list: windows with at least one dense tile
+    assert P["n_dwin"] == int(np.count_nonzero(np.diff(P["win_dptr"]))) if P["n_win"] else P["n_dwin"] == 0
+    # rows extracted by the row stage are exactly the rows with Len <= tau_row (Eq. 5)
+    if tau != INF:
+        lens = np.diff(rp)
+        assert np.array_equal(np.sort(P["aic_rows"]), np.nonzero(lens > t["tau_row"])[0])
+    else:
+        assert P["m_aic"] == 0 and P["n_res"] == A.nnz
 
 
 def _plan_product(A, P, B, b_bf16=False):
@@ -181,8 +159,8 @@ def _plan_product(A, P, B, b_bf16=False):
 
 
 MED_TUNES = [dict(tau_tile=INF), dict(tau_tile=1), dict(tau_tile=24, TM=16, TK=16),
-             dict(tau_tile=200, TM=32, TK=16, tau_row=4, chunk_nnz=64),
-             dict(tau_tile=64, TM=64, TK=32, tau_col=1, col_order=1, absorb_cap=16),
+             dict(tau_tile=200, TM=32, TK=16, tau_row=4),
+             dict(tau_tile=64, TM=64, TK=32, tau_col=1, col_order=1),
              dict(tau_tile=24, TM=16, TK=16, reorder=4)]
 
 
@@ -237,8 +215,8 @@ def test_attention_windows_are_full_tiles():
     nb = np.diff(P["dtile_voff"])
     assert np.all(nb == 256)                          # only full 16x16 tiles are dense
     assert P["n_res"] == A["m"]                       # one scattered nonzero per row remains
-    assert np.all(P["dwin_absorb"] == 1)
-    assert P["n_rl"] == 0 and P["n_split"] == 0
+    assert np.array_equal(np.diff(P["res_rowptr"]), np.ones(A["m"], np.int32))
+    assert P["n_dwin"] == P["n_win"] == A["m"] // 16  # every window holds dense tiles
 
 
 def test_invalid_csr_rejected():

@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 import synth
+from parity import check_result
 
 pytestmark = pytest.mark.gpu
 
@@ -34,17 +35,24 @@ def _static(At, A, Bt, C, K, dtype):
                                      ctypes.c_void_p(C.data_ptr()), K, K, dtype, s)
 
 
-@pytest.mark.parametrize("K,dtype", [(64, ns.NS_F32), (128, ns.NS_F32), (32, ns.NS_BF16)])
+def _dev(A):
+    return {k: (torch.from_numpy(v).to(DEV) if isinstance(v, np.ndarray) else v) for k, v in A.items()}
+
+
+def _b(B, dtype):
+    if dtype == ns.NS_BF16:
+        Bh = synth.bf16_bits(B)
+        return Bh, torch.from_numpy(Bh.view(np.int16)).to(DEV).view(torch.bfloat16)
+    return B, torch.from_numpy(B).to(DEV)
+
+
+@pytest.mark.parametrize("K,dtype", [(8, ns.NS_F32), (64, ns.NS_F32), (128, ns.NS_F32), (512, ns.NS_F32),
+                                     (1024, ns.NS_F32), (8, ns.NS_BF16), (32, ns.NS_BF16)])
 def test_static_matches_planned_path(K, dtype):
     A = synth.rmat_csr(13, 120000, seed=K)       # power-law rows: long rows are cut into pieces
     B = synth.dense_b(A["n"], K, seed=1)
-    At = {k: (torch.from_numpy(v).to(DEV) if isinstance(v, np.ndarray) else v) for k, v in A.items()}
-    if dtype == ns.NS_BF16:
-        Bh = synth.bf16_bits(B)
-        Bt = torch.from_numpy(Bh.view(np.int16)).to(DEV).view(torch.bfloat16)
-    else:
-        Bh = B
-        Bt = torch.from_numpy(B).to(DEV)
+    At = _dev(A)
+    Bh, Bt = _b(B, dtype)
     C_ref = torch.empty((A["m"], K), device=DEV)
     with ns.spmm_plan(At, K, dtype) as p:
         p.execute(Bt, C_ref)
@@ -58,8 +66,40 @@ def test_static_matches_planned_path(K, dtype):
         got = C.cpu().numpy()
         assert not np.isnan(got).any()
         assert oracle.rel_frobenius(got, ref) <= 1e-5
-    exact = oracle.spmm(A, Bh, b_bf16=dtype == ns.NS_BF16)
-    assert oracle.rel_frobenius(got, exact) <= 1e-5
+    check_result(got, A, Bh, b_bf16=dtype == ns.NS_BF16, tol=1e-5)
+
+
+def test_static_large_then_small():
+    # a small call right after a large one must not see the counters the large one left behind
+    big = synth.rmat_csr(15, 600000, seed=3)
+    small = synth.random_csr(300, 200, 0.05, seed=4, hub_rows=3, empty_rows=0.3)
+    for A in (big, small, big, small):
+        B = synth.dense_b(A["n"], 64, seed=5)
+        At, Bt = _dev(A), torch.from_numpy(B).to(DEV)
+        C = torch.full((A["m"], 64), float("nan"), device=DEV)
+        assert _static(At, A, Bt, C, 64, ns.NS_F32) == 0, ns.lib.ns_last_error()
+        torch.cuda.synchronize()
+        check_result(C.cpu().numpy(), A, B, tol=1e-5)
+
+
+@pytest.mark.parametrize("kind", ["no_nonzeros", "empty_rows", "no_rows"])
+def test_static_degenerate(kind):
+    if kind == "no_nonzeros":
+        A = synth.random_csr(100, 50, 0.0, seed=1)
+    elif kind == "empty_rows":
+        A = synth.random_csr(500, 80, 0.02, seed=2, empty_rows=0.7)
+    else:
+        A = synth.random_csr(0, 50, 0.0, seed=3)
+    B = synth.dense_b(A["n"], 16, seed=6)
+    At, Bt = _dev(A), torch.from_numpy(B).to(DEV)
+    C = torch.full((max(A["m"], 1), 16), float("nan"), device=DEV)
+    assert _static(At, A, Bt, C, 16, ns.NS_F32) == 0, ns.lib.ns_last_error()
+    torch.cuda.synchronize()
+    got = C.cpu().numpy()[:A["m"]]
+    if A["m"]:
+        check_result(got, A, B, tol=1e-5)
+    if A.nnz == 0:
+        assert np.all(got == 0)
 
 
 def test_static_rejects_oversized():

@@ -307,6 +307,7 @@ def main():
     ap.add_argument("--tn", type=int, default=None, help="override the column-slice width TN")
     ap.add_argument("--chunk", type=int, default=None, help="override the residual chunk size W")
     ap.add_argument("--tm", type=int, default=None, choices=[16, 32, 64], help="override the window height TM")
+    ap.add_argument("--tk", type=int, default=None, choices=[16, 32], help="override the tile width TK")
     ap.add_argument("--reorder", type=int, default=None,
                     help="Section 6.1 local reordering: windows per cluster (0 = off)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
@@ -406,6 +407,9 @@ def main():
     if args.tm is not None:
         tune.TM = args.tm
         tune_src += f", TM={args.tm}"
+    if args.tk is not None:
+        tune.TK = args.tk
+        tune_src += f", TK={args.tk}"
     if args.reorder is not None:
         tune.reorder = args.reorder
         tune_src += f", reorder={args.reorder}"

@@ -146,11 +146,15 @@ ns_status_t ns_release_cache(void);
 
 ns_status_t ns_plan_stats(ns_plan_t p, ns_plan_stats_t* st);
 
-/* Copy one named plan array to host memory (for bit-exact comparison with the CPU reference
- * partition).  Names: aic_rows win_rows win_dptr dwin dwin_absorb dtile_cols dtile_bits
- * dtile_voff dtile_vals res_rowptr res_col res_val rl_rows rl_start chunk_b chunk_k0 row_split
- * split_row split_np split_slot split_base queue item_cost.  ns_plan_array_info gives the element
- * count and size; `bytes` must be at least count * esize.  Synchronous. */
+/* Copy one named plan array to host memory (for comparison with the CPU reference partition and
+ * checks of the execute bookkeeping).  Names: aic_rows win_rows win_dptr dwin dwin_absorb
+ * dtile_cols dtile_bits dtile_voff dtile_vals dtile_x res_rowptr res_col res_val rl_rows rl_start
+ * chunk_b chunk_k0 row_split split_row split_np split_slot split_base queue item_cost.  The
+ * partition (Sections 5.2.2, 6.1) is aic_rows, win_rows, win_dptr, dtile_cols, dtile_bits,
+ * dtile_voff, dtile_vals and res_*; dtile_x (BF16 plans) holds every dense tile expanded to
+ * TM x TK BF16 values in 8 x 8 blocks of 128 bytes (the tensor cores' operand layout); the rest
+ * schedules the execute launch.  ns_plan_array_info gives the element count and size; `bytes`
+ * must be at least count * esize.  Synchronous. */
 ns_status_t ns_plan_array_info(ns_plan_t p, const char* name, int64_t* count, int32_t* esize);
 ns_status_t ns_plan_export(ns_plan_t p, const char* name, void* host_dst, int64_t bytes);
 

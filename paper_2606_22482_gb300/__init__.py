@@ -21,7 +21,7 @@ __all__ = ["NS_F32", "NS_BF16", "NS_TAU_INF", "NsError", "Tune", "PlanStats", "P
            "PLAN_ARRAYS"]
 
 PLAN_ARRAYS = ("aic_rows", "win_rows", "win_dptr", "dwin", "dwin_absorb", "dtile_cols",
-               "dtile_bits", "dtile_voff", "dtile_vals", "res_rowptr", "res_col", "res_val",
+               "dtile_bits", "dtile_voff", "dtile_vals", "dtile_x", "res_rowptr", "res_col", "res_val",
                "rl_rows", "rl_start", "chunk_b", "chunk_k0", "row_split", "split_row",
                "split_np", "split_slot", "split_base", "queue", "item_cost")
 
@@ -79,6 +79,8 @@ class Plan:
         check(lib.ns_plan_array_info(self._h, name.encode(), ctypes.byref(cnt), ctypes.byref(es)))
         if name == "dtile_vals":
             dt = np.uint16 if es.value == 2 else np.float32
+        elif name == "dtile_x":
+            dt = np.uint16
         elif name == "dtile_bits":
             dt = np.uint32
         elif name == "res_val":

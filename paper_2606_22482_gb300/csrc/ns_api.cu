@@ -361,6 +361,7 @@ static bool find_array(Plan* P, const char* name, ArrayRef* a)
     A(dtile_bits, P->dtile_bits, s.n_dtiles * BW, 4)
     A(dtile_voff, P->dtile_voff, s.n_dtiles + 1, 4)
     A(dtile_vals, P->dtile_vals, s.n_dvals, s.b_bf16 ? 2 : 4)
+    A(dtile_x, P->dtile_x, s.b_bf16 ? s.n_dtiles * TM * TK : 0, 2)
     A(res_rowptr, P->res_rowptr, s.m + 1, 4)
     A(res_col, P->res_col, s.n_res, 4)
     A(res_val, P->res_val, s.n_res, 4)

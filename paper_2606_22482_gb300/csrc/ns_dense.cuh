@@ -86,6 +86,7 @@ inline ns_status_t dense_prepare(const void* kern, size_t smem)
         return NS_ERR_UNSUPPORTED;
     }
     NS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    NS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     return NS_OK;
 }
 
@@ -131,9 +132,13 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo)
     lo = to_tf32(x - __uint_as_float(hi));
 }
 
+template <int L, int VPL, bool BF16, bool HINT>
+__device__ void dense_deliver_rows(const ExecDesc& D, int32_t di, int32_t w, float* Cs, int cs_stride,
+                                   int4* meta, const Policies& pol);
+
 // ---------------------------------------------------------------------------------------------
 template <int L, int VPL, bool BF16, bool HINT>
-__device__ void dense_item(const ExecDesc& D, int32_t di, unsigned char* smem, const Policies& pol)
+__device__ void dense_item(const ExecDesc& D, int32_t di, unsigned char* smem, int4* meta, const Policies& pol)
 {
     const int TM = D.TM, TK = D.TK, K = D.K;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -239,6 +244,12 @@ __device__ void dense_item(const ExecDesc& D, int32_t di, unsigned char* smem, c
                     }
                 }
             } else {
+                // The tensor pipe's FP32 accumulation is not round-to-nearest; a long chain of
+                // tiles into one accumulator drifts.  Each tile's products go to a fresh
+                // accumulator that is then added to the window's sum with an ordinary FP32 add.
+                float part[kDenseMaxNB][4];
+#pragma unroll
+                for (int nb = 0; nb < kDenseMaxNB; ++nb) part[nb][0] = part[nb][1] = part[nb][2] = part[nb][3] = 0.f;
                 const float* As = reinterpret_cast<const float*>(smem + G.off_a);
                 const float* Bs = reinterpret_cast<const float*>(smem + G.off_b[cur]);
                 for (int kk = 0; kk < TK; kk += 8) {
@@ -255,12 +266,16 @@ __device__ void dense_item(const ExecDesc& D, int32_t di, unsigned char* smem, c
                             uint32_t bhi0, blo0, bhi1, blo1;
                             split_tf32(br[0], bhi0, blo0);
                             split_tf32(br[4 * G.b_stride], bhi1, blo1);
-                            mma_tf32(acc[nb], alo, bhi0, bhi1);
-                            mma_tf32(acc[nb], ahi, blo0, blo1);
-                            mma_tf32(acc[nb], ahi, bhi0, bhi1);
+                            mma_tf32(part[nb], alo, bhi0, bhi1);
+                            mma_tf32(part[nb], ahi, blo0, blo1);
+                            mma_tf32(part[nb], ahi, bhi0, bhi1);
                         }
                     }
                 }
+#pragma unroll
+                for (int nb = 0; nb < kDenseMaxNB; ++nb)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[nb][e] += part[nb][e];
             }
             __syncthreads();  // buffer cur may be restaged for tile t + 2
         }
@@ -279,31 +294,135 @@ __device__ void dense_item(const ExecDesc& D, int32_t di, unsigned char* smem, c
         }
     }
     __syncthreads();
+    dense_deliver_rows<L, VPL, BF16, HINT>(D, di, w, Cs, G.cs_stride, meta, pol);
+}
 
-    // rows: tensor-core part + absorbed residual (CUDA cores), then delivery
+// The window's rows: the tensor-core part (Cs, TM x K FP32 in shared memory) plus the rows'
+// absorbed residual on the CUDA cores, then delivery (stored, or piece 0 of a split row).
+// Latency first: one pass loads every row's id, residual range and split id (a thread per row,
+// into `meta`); then each warp takes its rows (r = warp, warp + 4, ...) and gathers all of their
+// residual nonzeros as one list, 32 entries per load and four B rows in flight, adding them into
+// the rows of Cs it owns; last, the rows are delivered from Cs.
+template <int L, int VPL, bool BF16, bool HINT>
+__device__ void dense_deliver_rows(const ExecDesc& D, int32_t di, int32_t w, float* Cs, int cs_stride,
+                                   int4* meta, const Policies& pol)
+{
+    const int TM = D.TM, K = D.K;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool absorb = __ldg(D.dwin_absorb + di) != 0;
     const int nv = K >> 2;
     const int grp = lane / L, li = lane % L;
-    for (int r = warp; r < TM; r += kExecWarps) {
-        const int32_t i = __ldg(D.win_rows + (int64_t)w * TM + r);
-        if (i < 0) continue;
+    // ---- row metadata: (row id, first residual nonzero, residual length, split id) ----
+    for (int r = threadIdx.x; r < TM; r += kExecThreads) {
+        int32_t i = __ldg(D.win_rows + (int64_t)w * TM + r);
+        int32_t z0 = 0, n = 0, sp = -1;
         if (i >= D.m) {  // guard: corrupt plan
-            if (lane == 0) atomicOr(D.status, kStatusInternal);
-            continue;
+            atomicOr(D.status, kStatusInternal);
+            i = -1;
         }
+        if (i >= 0) sp = __ldg(D.row_split + i);
+        if (i >= 0 && absorb) {
+            z0 = __ldg(D.res_rowptr + i);
+            const int32_t z1 = __ldg(D.res_rowptr + i + 1);
+            n = z1 - z0;
+            if (z0 < 0 || n < 0 || (int64_t)z0 + n > D.n_res) {  // guard: corrupt plan
+                atomicOr(D.status, kStatusInternal);
+                n = 0;
+            }
+        }
+        meta[r] = make_int4(i, z0, n, sp);
+    }
+    __syncthreads();
+    // ---- absorbed residual: this warp's rows as one list of nonzeros ----
+    const int nrw = (TM - warp + kExecWarps - 1) / kExecWarps;  // rows warp, warp + 4, ... (<= 16)
+    int len = 0, z0l = 0;
+    if (lane < nrw) {
+        const int4 mt = meta[warp + kExecWarps * lane];
+        len = mt.z;
+        z0l = mt.y;
+    }
+    int start = len;  // inclusive scan over the warp's rows
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, start, o);
+        if (lane >= o) start += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, start, 15);
+    start -= len;  // exclusive
+    for (int e0 = 0; e0 < total; e0 += 32) {
+        // entry e0 + lane: its row l (largest l with start_l <= e), then its column and value
+        const int e = e0 + lane;
+        int l = 0;
+#pragma unroll
+        for (int step = 8; step >= 1; step >>= 1) {
+            const int s_l = __shfl_sync(0xffffffffu, start, (l + step) & 31);
+            if (l + step < nrw && s_l <= e) l += step;
+        }
+        const int zl = __shfl_sync(0xffffffffu, z0l, l & 31);
+        const int sl = __shfl_sync(0xffffffffu, start, l & 31);
+        int32_t ec = -1;
+        float ev = 0.f;
+        if (e < total) {
+            const int64_t z = (int64_t)zl + (e - sl);
+            ec = __ldg(D.res_col + z);
+            ev = __ldg(D.res_val + z);
+            if ((unsigned)ec >= (unsigned)D.n) {  // guard: never gather outside B
+                atomicOr(D.status, kStatusInternal);
+                ec = -1;
+            }
+        }
+        const int er = warp + kExecWarps * l;  // the entry's row in the window
+        const int cnt = total - e0 < 32 ? total - e0 : 32;
+        // the warp gathers the listed B rows, four in flight, lanes across the row
+        for (int j0 = 0; j0 < cnt; j0 += 4) {
+            BRaw<BF16> b[4][VPL];
+            float val[4];
+            int row[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + u;
+                const int32_t col = __shfl_sync(0xffffffffu, ec, j & 31);
+                val[u] = __shfl_sync(0xffffffffu, ev, j & 31);
+                row[u] = __shfl_sync(0xffffffffu, er, j & 31);
+                const bool have = j < cnt && col >= 0;
+                if (!have) val[u] = 0.f;
+#pragma unroll
+                for (int q = 0; q < VPL; ++q) {
+                    const int v = li + L * q;
+                    const int64_t off = (int64_t)(have ? col : 0) * D.ldb + 4 * v;
+                    b[u][q] = (have && grp == 0 && v < nv)
+                                  ? ld_braw<BF16, HINT>(static_cast<const unsigned char*>(D.B) + off * (BF16 ? 2 : 4), pol.last)
+                                  : braw_zero<BF16>();
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (j0 + u >= cnt) break;
+#pragma unroll
+                for (int q = 0; q < VPL; ++q) {
+                    const int v = li + L * q;
+                    if (grp == 0 && v < nv) {
+                        float4* cp = reinterpret_cast<float4*>(Cs + row[u] * cs_stride + 4 * v);
+                        *cp = f4_fma(val[u], widen(b[u][q]), *cp);
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    // ---- delivery, a warp per row ----
+    for (int r = warp; r < TM; r += kExecWarps) {
+        const int4 mt = meta[r];
+        const int32_t i = mt.x;
+        if (i < 0) continue;
         float4 acc[VPL];
 #pragma unroll
         for (int q = 0; q < VPL; ++q) {
             const int v = li + L * q;
-            acc[q] = (grp == 0 && v < nv) ? *reinterpret_cast<const float4*>(Cs + r * G.cs_stride + 4 * v)
+            acc[q] = (grp == 0 && v < nv) ? *reinterpret_cast<const float4*>(Cs + r * cs_stride + 4 * v)
                                           : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (absorb) {
-            const int64_t z0 = __ldg(D.res_rowptr + i), z1 = __ldg(D.res_rowptr + i + 1);
-            gather_accumulate<L, VPL, BF16, HINT>(D, z0, z1, acc, lane, pol);
-        }
-        group_reduce<L, VPL>(acc);
-        deliver_row<L, VPL, HINT>(D, i, 0, true, acc, lane, pol.first);
+        deliver_row<L, VPL, HINT>(D, i, 0, true, acc, lane, pol.first, mt.w);
     }
     __syncthreads();  // shared memory is reused by the next item
 }

@@ -142,13 +142,15 @@ __device__ __forceinline__ float4 f4_add(float4 a, float4 b)
 // delivering one piece of an output row
 //   L lanes (lane < L) hold VPL float4 vectors each: vector v = lane + L*q covers columns 4v..4v+3
 // ---------------------------------------------------------------------------------------------
+// `split`: the row's split id when the caller has it (>= -1), else kSplitUnknown (loaded here)
+constexpr int32_t kSplitUnknown = -2;
 template <int L, int VPL, bool HINT>
 __device__ __forceinline__ void deliver_row(const ExecDesc& D, int32_t row, int32_t piece_of_chunk,
                                             bool dense_piece, const float4 (&acc)[VPL], int lane,
-                                            uint64_t pol_first)
+                                            uint64_t pol_first, int32_t split = kSplitUnknown)
 {
     const int nv = D.K >> 2;
-    const int32_t s = __ldg(D.row_split + row);
+    const int32_t s = split != kSplitUnknown ? split : __ldg(D.row_split + row);
     float* crow = D.C + (int64_t)row * D.ldc;
     if (s < 0) {
         if (lane < L) {
@@ -613,6 +615,7 @@ __device__ void residual_chunk(const ExecDesc& D, int32_t c, int lane, const Pol
 }  // namespace ns
 
 #include "ns_dense.cuh"
+#include "ns_dense_tc.cuh"
 
 namespace ns {
 
@@ -637,12 +640,20 @@ __global__ void __launch_bounds__(kExecThreads, DENSE ? 1 : 4) k_exec(const Exec
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int32_t s_ticket;
+    __shared__ int4 s_rowmeta[DENSE ? 64 : 1];  // a dense window's rows (TM <= 64)
+    // BF16 plans with K <= 256 run their dense tiles on the 5th-generation tensor cores (tcgen05,
+    // accumulator in tensor memory); other dense plans use the warp-level mma.sync item
+    constexpr bool TC = DENSE && BF16 && VPL <= 2;
+    __shared__ __align__(8) uint64_t s_tc_bars[TC ? kTcBars : 1];
+    __shared__ uint32_t s_tc_tmem;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Policies pol{0, 0};
     if (HINT) pol = make_policies();
     unsigned long long* const clk = descs ? nullptr : d0.class_clock;  // single-plan launches only
     if (clk && threadIdx.x == 0) atomicMin(clk, global_ns());
     if (DENSE) {
+        TcState tcs{};
+        if constexpr (TC) tc_setup(tcs, s_tc_bars, &s_tc_tmem);
         // phase 1: dense windows, one CTA each, taken in work-list order
         for (;;) {
             if (threadIdx.x == 0) s_ticket = atomicAdd(ctrl + 0, 1);
@@ -653,13 +664,29 @@ __global__ void __launch_bounds__(kExecThreads, DENSE ? 1 : 4) k_exec(const Exec
             const int32_t it = __ldg(queue + t);
             const ExecDesc& D = descs ? descs[queue_desc ? __ldg(queue_desc + t) : 0] : d0;
             if (it < D.n_dwin) {
-                if (dynamic_smem_bytes() >= (uint32_t)dense_geom(D.K, D.TM, D.TK, BF16).total)
-                    dense_item<L, VPL, BF16, HINT>(D, it, smem_raw, pol);
-                else if (threadIdx.x == 0)
-                    atomicOr(D.status, kStatusInternal);  // guard: launch without the tile buffers
+                if constexpr (TC) {
+                    const TcGeom G = tc_geom(D.K, D.TM, D.TK);
+                    if (!tcs.ok) {
+                        // an earlier bounded wait of this CTA gave up (status already set)
+                    } else if (dynamic_smem_bytes() >= (uint32_t)G.total && tc_supported(D.K) && D.dtile_x &&
+                               D.TM % 16 == 0 && D.TM <= 64 && D.TK % 16 == 0) {
+                        const int32_t w = __ldg(D.dwin + it);
+                        if (tc_window_product<HINT>(D, w, smem_raw, G, tcs, pol))
+                            dense_deliver_rows<L, VPL, BF16, HINT>(D, it, w, reinterpret_cast<float*>(smem_raw + G.off_c),
+                                                                  G.cs_stride, s_rowmeta, pol);
+                    } else if (threadIdx.x == 0) {
+                        atomicOr(D.status, kStatusInternal);  // guard: launch without the tile buffers
+                    }
+                } else {
+                    if (dynamic_smem_bytes() >= (uint32_t)dense_geom(D.K, D.TM, D.TK, BF16).total)
+                        dense_item<L, VPL, BF16, HINT>(D, it, smem_raw, s_rowmeta, pol);
+                    else if (threadIdx.x == 0)
+                        atomicOr(D.status, kStatusInternal);  // guard: launch without the tile buffers
+                }
                 if (clk && threadIdx.x == 0) atomicMax(clk + 1, global_ns());
             }
         }
+        if constexpr (TC) tc_teardown(tcs, descs ? descs[0].status : d0.status);
     }
     // phase 2: residual chunks, one warp each, in work-list order (no CTA barrier)
     for (;;) {
@@ -1034,6 +1061,7 @@ void fill_desc(const Plan* P, const void* B, int64_t ldb, float* C, int64_t ldc,
     d->dtile_bits = P->dtile_bits;
     d->dtile_voff = P->dtile_voff;
     d->dtile_vals = P->dtile_vals;
+    d->dtile_x = P->dtile_x;
     d->row_split = P->row_split;
     d->split_np = P->split_np;
     d->split_slot = P->split_slot;
@@ -1145,7 +1173,8 @@ static size_t exec_smem_bytes(int K, int TM, int TK, bool bf16, bool dense, int 
     size_t b = staged_path(L, VPL) ? (size_t)kExecWarps * stage_geom(K, bf16, W).warp_bytes : 0;
     // (chunk_nnz <= 1024 keeps this within the 227 KB a CTA may use)
     if (dense) {
-        size_t d = dense_smem_bytes(K, TM, TK, bf16);
+        // BF16 with K <= 256: the tensor-core (tcgen05) item's ring; otherwise the mma.sync item
+        size_t d = (bf16 && VPL <= 2) ? (size_t)tc_geom(K, TM, TK).total : dense_smem_bytes(K, TM, TK, bf16);
         if (d > b) b = d;
     }
     return b;
@@ -1161,9 +1190,22 @@ ns_status_t exec_prepare(int64_t n_items, int K, int TM, int TK, bool bf16, bool
     if (smem > 48 * 1024) NS_TRY(dense_prepare(reinterpret_cast<const void*>(kern), smem));
     int per_sm = 0;
     NS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kExecThreads, smem));
-    if (per_sm < 1) per_sm = 1;
     int dev = 0;
     NS_CUDA_TRY(cudaGetDevice(&dev));
+    if (smem > 48 * 1024) {
+        // The query may assume a smaller shared-memory carve-out than the SM has; the persistent
+        // grid is sized from the SM's capacity (CTAs that do not fit simply start later).
+        int sm_smem = 0, regs_sm = 0;
+        cudaFuncAttributes fa{};
+        NS_CUDA_TRY(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        NS_CUDA_TRY(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+        NS_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+        const int by_smem = sm_smem / (int)(smem + fa.sharedSizeBytes + 1024);
+        const int by_regs = fa.numRegs > 0 ? regs_sm / (fa.numRegs * kExecThreads) : by_smem;
+        const int fit = by_smem < by_regs ? by_smem : by_regs;
+        if (fit > per_sm) per_sm = fit;
+    }
+    if (per_sm < 1) per_sm = 1;
     int64_t g = (int64_t)per_sm * num_sms(dev);
     if (g > n_items) g = n_items;
     *grid_out = (int)(g > 0 ? g : 1);

@@ -127,6 +127,7 @@ struct ExecDesc {
     const uint32_t* dtile_bits;
     const int32_t* dtile_voff;
     const void* dtile_vals;
+    const uint16_t* dtile_x;  // BF16 plans: every dense tile expanded, in the tensor-core layout
     // split rows
     const int32_t* row_split;
     const int32_t* split_np;
@@ -175,6 +176,7 @@ struct Plan {
     uint32_t* dtile_bits = nullptr;
     int32_t* dtile_voff = nullptr;
     void* dtile_vals = nullptr;
+    uint16_t* dtile_x = nullptr;  // BF16 plans: dense tiles expanded (execution format, see k_emit_tiles)
     const int32_t* res_rowptr = nullptr;  // aliases rowptr when nothing is dense
     const int32_t* res_col = nullptr;
     const float* res_val = nullptr;

@@ -620,7 +620,18 @@ struct EmitArgs {
     int32_t* dtile_voff;
     void* dtile_vals;
     uint8_t* pdense;  // per original element: 1 if in a dense tile
+    uint16_t* dtile_x;  // BF16 plans: each dense tile expanded to TM x TK values (zeros included)
 };
+
+// Position of element (row r, compacted column c) inside an expanded TM x TK tile: 8 x 8 blocks
+// of 128 contiguous bytes (8 rows of 8 consecutive columns), the blocks of a row group side by
+// side along the columns, row groups one after another.  This is the no-swizzle K-major operand
+// layout of the tensor core's shared-memory descriptors (K = compacted columns, N = rows), so
+// the execute kernel copies a tile into shared memory as one contiguous block.
+__host__ __device__ __forceinline__ int tile_x_offset(int r, int c, int TK)
+{
+    return (r >> 3) * (TK >> 3) * 64 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7);
+}
 
 __global__ void __launch_bounds__(kWinThreads) k_emit_tiles(EmitArgs a)
 {
@@ -728,7 +739,10 @@ __global__ void __launch_bounds__(kWinThreads) k_emit_tiles(EmitArgs a)
             const float v = __ldg(a.vals + p);
             if (a.bf16) {
                 __nv_bfloat16 h = __float2bfloat16_rn(v);
-                reinterpret_cast<uint16_t*>(a.dtile_vals)[vi] = *reinterpret_cast<uint16_t*>(&h);
+                const uint16_t hb = *reinterpret_cast<uint16_t*>(&h);
+                reinterpret_cast<uint16_t*>(a.dtile_vals)[vi] = hb;
+                if (a.dtile_x)
+                    a.dtile_x[(int64_t)(dbase + k) * TM * TK + tile_x_offset(r, pos % TK, TK)] = hb;
             } else {
                 reinterpret_cast<float*>(a.dtile_vals)[vi] = v;
             }
@@ -1061,6 +1075,7 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
     pb.reserve_bytes(&P->dtile_vals, (size_t)(n_dvals > 0 ? n_dvals : 1) * (bf16 ? 2 : 4));
     pb.reserve(&P->res_col_own, n_res);
     pb.reserve(&P->res_val_own, n_res);
+    if (bf16) pb.reserve(&P->dtile_x, n_dtiles * TM * TK);
     NS_TRY(pb.commit(s));
     P->blocks.push_back(pb.take());
     P->res_col = P->res_col_own;
@@ -1068,6 +1083,8 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
     NS_CUDA_TRY(cudaMemsetAsync(P->dtile_bits, 0, sizeof(uint32_t) * (n_dtiles * BW > 0 ? n_dtiles * BW : 1), s));
     NS_CUDA_TRY(cudaMemsetAsync(P->dtile_vals, 0, (size_t)(n_dvals > 0 ? n_dvals : 1) * (bf16 ? 2 : 4), s));
     NS_CUDA_TRY(cudaMemsetAsync(pdense, 0, (size_t)(nnz > 0 ? nnz : 1), s));
+    if (bf16 && n_dtiles > 0)
+        NS_CUDA_TRY(cudaMemsetAsync(P->dtile_x, 0, sizeof(uint16_t) * n_dtiles * TM * TK, s));
     {
         int32_t v32 = (int32_t)n_dvals;
         NS_CUDA_TRY(cudaMemcpyAsync(P->dtile_voff + n_dtiles, &v32, sizeof v32, cudaMemcpyHostToDevice, s));
@@ -1075,7 +1092,7 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
     if (n_dtiles > 0) {
         EmitArgs ea{row_kbase, eidx, epos, ucan, trank, tvoff, win_U, win_ndt, P->win_dptr, win_vbase,
                     P->vals, m_aic, TM, TK, bf16 ? 1 : 0, P->dtile_cols, P->dtile_bits, P->dtile_voff,
-                    P->dtile_vals, pdense};
+                    P->dtile_vals, pdense, bf16 ? P->dtile_x : nullptr};
         k_emit_tiles<<<(unsigned)n_win, kWinThreads, 0, s>>>(ea);
         NS_LAUNCH_CHECK();
     }

@@ -161,9 +161,38 @@ def check_bookkeeping(A: dict, part: dict, st: dict, ex: dict, tune: dict) -> No
     assert np.all(np.diff(q)[same] > 0), "ties not in item order"
 
 
+def tile_x_offsets(TM: int, TK: int) -> np.ndarray:
+    """Element offset of (row r, column c) of a TM x TK tile in the expanded tile layout: 8 x 8
+    blocks of 64 consecutive elements (8 rows of 8 columns), blocks of a row group side by side
+    along the columns, row groups one after another."""
+    r = np.arange(TM)[:, None]
+    c = np.arange(TK)[None, :]
+    return ((r // 8) * (TK // 8) * 64 + (c // 8) * 64 + (r % 8) * 8 + (c % 8)).reshape(-1)
+
+
+def check_expanded_tiles(part: dict, x: np.ndarray) -> None:
+    """BF16 plans: every dense tile expanded (zeros where the bitmap is clear) equals dtile_x."""
+    nd, TM, TK = int(part["n_dtiles"]), int(part["TM"]), int(part["TK"])
+    assert x.dtype == np.uint16 and x.size == nd * TM * TK, "expanded tiles: size"
+    if nd == 0:
+        return
+    bits = np.unpackbits(part["dtile_bits"].reshape(nd, -1).view(np.uint8), axis=1, bitorder="little")
+    bits = bits[:, :TM * TK].astype(bool)                      # bit r * TK + c
+    rank = np.cumsum(bits, axis=1) - 1                         # value index inside the tile
+    voff = part["dtile_voff"].astype(np.int64)[:-1]
+    vals = part["dtile_vals"]
+    dense = np.zeros((nd, TM * TK), np.uint16)
+    dense[bits] = vals[(voff[:, None] + rank)[bits]]
+    expect = np.zeros((nd, TM * TK), np.uint16)
+    expect[:, tile_x_offsets(TM, TK)] = dense
+    assert np.array_equal(x.reshape(nd, -1), expect), "expanded tiles differ from bitmap + values"
+
+
 def compare_plan(plan, ref: dict, A: dict, tune) -> None:
     """The device plan's partition bit-exact with the oracle's, and its bookkeeping valid."""
     st = plan.stats()
     arrays = {name: plan.export(name) for name in oracle.PLAN_ARRAYS}
     compare_partition(st, arrays, ref)
     check_bookkeeping(A, ref, st, exports(plan), tune.as_dict())
+    if st["b_bf16"]:
+        check_expanded_tiles(ref, plan.export("dtile_x"))

@@ -205,7 +205,9 @@ def test_bookkeeping_checker_bites():
     # planted mistakes in each of its arrays
     from plan_checks import check_bookkeeping, exports
     A = synth.random_csr(400, 500, 0.03, seed=5, hub_rows=4, empty_rows=0.2)
-    t = tune_from(ns, tau_tile=6, TM=16, TK=16, chunk_nnz=16, absorb_cap=8)
+    # long rows kept for windows (tau_row), tiles dense only where columns repeat (tau 40), no
+    # absorption: the kept rows are assembled from a dense piece and residual chunk pieces
+    t = tune_from(ns, tau_tile=40, TM=16, TK=16, tau_row=20, chunk_nnz=16, absorb_cap=0)
     part = oracle.plan(A, 32, **oracle_tune(t))
     with ns.spmm_plan(to_dev(A, DEV), 32, ns.NS_F32, t) as p:
         st, ex = p.stats(), exports(p)
@@ -226,7 +228,13 @@ def test_bookkeeping_checker_bites():
     def drop_rl(e):
         e["rl_rows"] = e["rl_rows"][:-1].copy()
 
-    mutations = [bump("chunk_b", 1), bump("chunk_k0", 1), bump("split_base", 0), bump("split_slot", 1),
+    def empty_chunk(e):
+        e["chunk_b"] = e["chunk_b"].copy()
+        e["chunk_b"][1] = e["chunk_b"][0]
+
+    # (moving a boundary by one inside a long row is not a mistake: the pieces stay consistent)
+    mutations = [empty_chunk, bump("chunk_b", -1, -1), bump("chunk_k0", 1), bump("split_base", 0),
+                 bump("split_slot", 0),
                  bump("split_np", 0), bump("row_split", int(np.argmax(ex["row_split"] < 0)), 1),
                  bump("dwin_absorb", 0), bump("rl_start", 2), bump("item_cost", 0, 1 << 20),
                  swap_queue, drop_rl]

@@ -61,3 +61,28 @@ def test_bf16_tiles_need_their_allowance(case):
     check_result(C, A, B, bf16_tiles=True, tol=2e-2, threads=1)
     with pytest.raises(AssertionError):
         check_result(C, A, B, bf16_tiles=False, tol=2e-2, threads=1)
+
+
+def test_expanded_tile_check_on_the_oracle_partition():
+    # the expanded-tile layout check, on an expansion written here element by element
+    import oracle
+    from plan_checks import check_expanded_tiles
+    A = synth.block_sparse_csr(256, seed=4, block=16, band=2, p_random=0.1)
+    for TM, TK in ((16, 16), (32, 16), (16, 32), (64, 32)):
+        P = oracle.plan(A, 16, b_bf16=True, tau_tile=40, TM=TM, TK=TK)
+        nd, BW = P["n_dtiles"], TM * TK // 32
+        assert nd > 0
+        x = np.zeros(nd * TM * TK, np.uint16)
+        for d in range(nd):
+            k = P["dtile_voff"][d]
+            for r in range(TM):
+                for c in range(TK):
+                    bit = r * TK + c
+                    if (P["dtile_bits"][d * BW + bit // 32] >> (bit % 32)) & 1:
+                        off = (r // 8) * (TK // 8) * 64 + (c // 8) * 64 + (r % 8) * 8 + c % 8
+                        x[d * TM * TK + off] = P["dtile_vals"][k]
+                        k += 1
+        check_expanded_tiles(P, x)
+        x[7] ^= 1
+        with pytest.raises(AssertionError):
+            check_expanded_tiles(P, x)

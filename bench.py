@@ -253,16 +253,27 @@ def run_cpu_oracle(A, B, K, seconds_budget: float, threads: int, bf16: bool = Fa
            "sample": f"{len(rows)} rows ({nnz_s} nnz, {nnz_s / A.nnz:.1%} of A), FP64, {dt:.2f} s",
            "cpu_model": cpu_model(),
            "single_thread": oracle_single_thread(A, B, K, bf16)}
-    acc = None
-    if C_gpu is not None:
-        diff = np.asarray(C_gpu[rows], dtype=np.float64) - ref
-        dn, rn = np.linalg.norm(diff, axis=1), np.linalg.norm(ref, axis=1)
-        nz = rn > 0
-        acc = {"rel_frobenius_vs_fp64": float(np.linalg.norm(dn) / max(np.linalg.norm(rn), 1e-300)),
-               "max_row_rel_err": float((dn[nz] / rn[nz]).max()) if nz.any() else 0.0,
-               "zero_rows_exact": bool(np.all(dn[~nz] == 0)),
-               "rows_checked": int(len(rows)), "of_rows": int(A["m"])}
+    acc = accuracy(A, C_gpu, rows, ref) if C_gpu is not None else None
     return out, acc
+
+
+def accuracy(A, C_gpu, rows, ref) -> dict:
+    """Error of the device result on `rows` against the FP64 oracle's values `ref` there."""
+    diff = np.asarray(C_gpu[rows], dtype=np.float64) - ref
+    dn, rn = np.linalg.norm(diff, axis=1), np.linalg.norm(ref, axis=1)
+    nz = rn > 0
+    return {"rel_frobenius_vs_fp64": float(np.linalg.norm(dn) / max(np.linalg.norm(rn), 1e-300)),
+            "max_row_rel_err": float((dn[nz] / rn[nz]).max()) if nz.any() else 0.0,
+            "zero_rows_exact": bool(np.all(dn[~nz] == 0)),
+            "rows_checked": int(len(rows)), "of_rows": int(A["m"])}
+
+
+def accuracy_sample(A, B, K, bf16: bool, C_gpu, threads: int, target_nnz: int = 400_000) -> dict:
+    """The device result against the FP64 oracle on a uniform row sample (no timing): the
+    accuracy figure of a bench line that skips the CPU baseline."""
+    import oracle
+    rows, _ = cpu_sample_rows(A, target_nnz, seed=11)
+    return accuracy(A, C_gpu, rows, oracle.spmm(A, B, rows=rows, threads=threads, b_bf16=bf16))
 
 
 def replicas_result(ms_step: float, flops_per_rank: float, ws: int, device) -> tuple:
@@ -298,8 +309,14 @@ def main():
     ap.add_argument("--rebalance", action="store_true",
                     help="choose tau by the epoch-level re-balance loop (Section 5.3) instead")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrivals per second")
-    ap.add_argument("--duration", type=float, default=5.0, help="serve: seconds of arrivals")
-    ap.add_argument("--pool", type=int, default=64, help="serve: graphs in the pool")
+    ap.add_argument("--duration", type=float, default=30.0, help="serve: seconds of arrivals")
+    ap.add_argument("--pool", type=int, default=1024, help="serve: graphs in the pool")
+    ap.add_argument("--inflight", type=int, default=256, help="serve: requests admitted at once")
+    ap.add_argument("--serve-budget", type=float, default=64.0, help="serve: HBM budget (GiB)")
+    ap.add_argument("--plain-requests", type=int, default=2000,
+                    help="serve: requests of the trace also run one at a time (plain path)")
+    ap.add_argument("--serve-checks", type=int, default=400,
+                    help="serve: about this many served results compared with the oracle")
     ap.add_argument("--tau", default="auto", help="'auto' (autotuner), 'inf' or an integer")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--l2", type=int, default=None, choices=[0, 1, 2],
@@ -495,6 +512,8 @@ def main():
     if not args.no_cpu:
         # the last timed step's C, read back after the timed region, against the FP64 oracle
         cpu, acc = run_cpu_oracle(A, B, K, 12.0, threads, bf16, C_gpu=Ct.cpu().numpy())
+    else:
+        acc = accuracy_sample(A, B, K, bf16, Ct.cpu().numpy(), threads)
     out = {
         "metric": METRIC,
         "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
@@ -682,117 +701,208 @@ def bench_gcn(args, threads):
 # ---------------------------------------------------------------------------------------------
 # served form: open-loop Poisson arrivals, continuous batching vs one request at a time
 # ---------------------------------------------------------------------------------------------
+def _serve_graph_job(args):
+    import synth
+    n, seed = args
+    return synth.serve_graph(int(n), seed=seed)
+
+
+def make_serve_pool(count: int, seed: int, workers: int):
+    """The serving pool: `count` RMAT graphs (lognormal node counts, median 20k, sigma 1.2, at
+    most 2M nodes, average degree 16), generated by a spawn-started process pool."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    import synth
+    sizes = synth.serve_pool_sizes(count, seed)
+    jobs = [(int(n), 1000 + i) for i, n in enumerate(sizes)]
+    order = np.argsort(-sizes)                   # largest first: the pool finishes together
+    out = [None] * count
+    with ProcessPoolExecutor(max_workers=max(1, workers), mp_context=mp.get_context("spawn")) as ex:
+        for i, g in zip(order, ex.map(_serve_graph_job, [jobs[i] for i in order], chunksize=1)):
+            out[i] = g
+    return sizes, out
+
+
+class PinnedPool:
+    """Page-locked float32 buffers for results, reused by power-of-two size class."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        self.free = {}
+
+    def get(self, m: int, K: int):
+        n = max(1, m * K)
+        cls = 1 << (n - 1).bit_length()
+        lst = self.free.setdefault(cls, [])
+        t = lst.pop() if lst else self.torch.empty(cls, dtype=self.torch.float32).pin_memory()
+        return t, t.numpy()[:m * K].reshape(m, K)
+
+    def put(self, t):
+        self.free.setdefault(t.numel(), []).append(t)
+
+
 def bench_serve(args, threads):
     import torch
     import oracle
-    import synth
     import paper_2606_22482_gb300 as ns
+    t_setup = time.perf_counter()
+    sizes, graphs = make_serve_pool(args.pool, args.seed, threads)
+    t_pool = time.perf_counter() - t_setup
     torch.cuda.set_device(0)
     rng = np.random.default_rng(args.seed)
-    sizes = synth.serve_pool_sizes(args.pool, args.seed)
-    graphs = [synth.serve_graph(int(n), seed=1000 + i) for i, n in enumerate(sizes)]
     n_req = int(args.rate * args.duration)
     arr = np.cumsum(rng.exponential(1.0 / args.rate, size=n_req))
     req_g = rng.integers(0, len(graphs), size=n_req)
     req_K = rng.choice([32, 64, 128], size=n_req)
     req_bf = rng.integers(0, 2, size=n_req).astype(bool)
-    # pinned operands: one B per (graph, K, dtype); a ring of C buffers per (graph, K)
-    Bbuf, Cring = {}, {}
-    ring = 8
-    for g, K, bf in set(zip(req_g.tolist(), req_K.tolist(), req_bf.tolist())):
-        b = synth.dense_b(graphs[g]["n"], K, seed=g * 7 + K)
-        if bf:
-            t = torch.from_numpy(synth.bf16_bits(b).view(np.int16)).pin_memory()
-            Bbuf[(g, K, bf)] = (t, t.numpy().view(np.uint16), b)
-        else:
-            t = torch.from_numpy(b).pin_memory()
-            Bbuf[(g, K, bf)] = (t, t.numpy(), b)
-        if (g, K) not in Cring:
-            Cring[(g, K)] = [torch.empty((graphs[g]["m"], K), dtype=torch.float32).pin_memory()
-                             for _ in range(ring)]
-    flops = float(sum(2.0 * graphs[g].nnz * K for g, K in zip(req_g, req_K)))
+    nnz = np.array([g.nnz for g in graphs], dtype=np.int64)
+    flops = float((2.0 * nnz[req_g] * req_K).sum())
+    # one pinned random block per dtype: the B of a request is its first n x K elements
+    max_el = int(max(g["n"] for g in graphs)) * 128
+    gen = torch.Generator().manual_seed(args.seed + 7)
+    Bf32 = torch.randn(max_el, generator=gen, dtype=torch.float32).pin_memory()
+    Bb16 = torch.randn(max_el, generator=gen, dtype=torch.float32).to(torch.bfloat16).pin_memory()
+    Bf32_np, Bb16_np = Bf32.numpy(), Bb16.view(torch.int16).numpy().view(np.uint16)
 
-    def run_served(max_inflight):
-        sv = ns.Server(hbm_budget_bytes=16 << 30, max_inflight=max_inflight, max_queue=1 << 16)
-        gids = [sv.register(g) for g in graphs]
-        # warm: plan every (graph, K, dtype) once so plans are resident (serving keeps them)
-        warm = []
-        for key in Bbuf:
-            g, K, bf = key
-            warm.append(sv.submit(gids[g], Bbuf[key][1], Cring[(g, K)][0].numpy(),
-                                  ns.NS_BF16 if bf else ns.NS_F32))
-        for t in warm:
-            while not sv.poll(t)[0]:
-                time.sleep(0.0002)
-        use = {k: 0 for k in Cring}
-        tickets = [None] * n_req
-        lat = np.zeros(n_req)
-        pending = {}
+    def b_of(i):
+        g, K = int(req_g[i]), int(req_K[i])
+        blk = Bb16_np if req_bf[i] else Bf32_np
+        return blk[:graphs[g]["n"] * K].reshape(graphs[g]["n"], K)
+
+    check_every = max(1, n_req // args.serve_checks)
+    check_rows = {}
+
+    def rows_to_check(i):
+        m = graphs[int(req_g[i])]["m"]
+        if m <= 2048:
+            return np.arange(m, dtype=np.int32)
+        return np.sort(np.random.default_rng(i).choice(m, 2048, replace=False)).astype(np.int32)
+
+    pool = PinnedPool()
+    tune = ns.tune_default()
+    sv = ns.Server(hbm_budget_bytes=int(args.serve_budget * (1 << 30)), max_inflight=args.inflight,
+                   max_queue=1 << 16, max_graphs=len(graphs) + 16, tune=tune)
+    gids = [sv.register(g) for g in graphs]
+    # warm: the planner builds every graph's plan once (one plan per graph serves every K and
+    # dtype under this tune); plans stay resident for the trace
+    t_w = ns.now()
+    warm = {}
+    for g in range(len(graphs)):
+        Ct, Cv = pool.get(graphs[g]["m"], 32)
+        warm[sv.submit(gids[g], Bf32_np[:graphs[g]["n"] * 32].reshape(-1, 32), Cv, ns.NS_F32)] = Ct
+    plan_wait = []
+    while warm:
+        for tk in list(warm):
+            done, st = sv.poll(tk)
+            if done:
+                pool.put(warm.pop(tk))
+                if st["t_planned"] > 0:
+                    plan_wait.append(st["t_planned"] - t_w)
+        time.sleep(0.0005)
+    t_warm = ns.now() - t_w
+
+    # ---- the timed trace ----
+    lat = np.zeros(n_req)
+    parts = np.zeros((n_req, 3))                # admission wait, launch, device + copies
+    out_rows = {}
+    pending = {}
+    launches0 = ns.launch_count()
+    with ClockSampler(0) as clk:
+        clk.start()
         t0 = ns.now()
         i = 0
         while i < n_req or pending:
             now = ns.now() - t0
             while i < n_req and arr[i] <= now:
                 g, K, bf = int(req_g[i]), int(req_K[i]), bool(req_bf[i])
-                Cb = Cring[(g, K)][use[(g, K)] % ring]
-                use[(g, K)] += 1
-                tk = sv.submit(gids[g], Bbuf[(g, K, bf)][1], Cb.numpy(), ns.NS_BF16 if bf else ns.NS_F32,
-                               t_arrival=t0 + arr[i])
-                pending[tk] = i
+                Ct, Cv = pool.get(graphs[g]["m"], K)
+                tk = sv.submit(gids[g], b_of(i), Cv, ns.NS_BF16 if bf else ns.NS_F32, t_arrival=t0 + arr[i])
+                pending[tk] = (i, Ct, Cv)
                 i += 1
             for tk in list(pending):
                 done, st = sv.poll(tk)
                 if done:
-                    j = pending.pop(tk)
-                    lat[j] = st["t_done"] - (t0 + arr[j])
-            time.sleep(0.00005)
+                    j, Ct, Cv = pending.pop(tk)
+                    ta = t0 + arr[j]
+                    lat[j] = st["t_done"] - ta
+                    parts[j] = (st["t_admit"] - ta, st["t_start"] - st["t_admit"], st["t_done"] - st["t_start"])
+                    if j % check_every == 0:
+                        r = rows_to_check(j)
+                        out_rows[j] = (r, Cv[r].copy())
+                    pool.put(Ct)
+            time.sleep(0.0001)
         wall = ns.now() - t0
-        sv.close()
-        return lat, wall
-
-    def run_plain():
-        """the same trace, one request at a time through ns_spmm_host (plan + execute + copies)"""
-        lat = np.zeros(n_req)
-        t0 = time.perf_counter()
-        for i in range(n_req):
-            now = time.perf_counter() - t0
-            if arr[i] > now:
-                time.sleep(arr[i] - now)
-            g, K, bf = int(req_g[i]), int(req_K[i]), bool(req_bf[i])
-            ns.spmm_host(graphs[g], Bbuf[(g, K, bf)][1], Cring[(g, K)][0].numpy(), ns.NS_BF16 if bf else ns.NS_F32)
-            lat[i] = time.perf_counter() - t0 - arr[i]
-        return lat, time.perf_counter() - t0
-
-    lat_s, wall_s = run_served(64)
-    lat_p, wall_p = run_plain()
-    # accuracy spot check of served results (fresh run of a few requests)
-    errs = []
-    sv = ns.Server(hbm_budget_bytes=16 << 30)
-    gids = [sv.register(g) for g in graphs]
-    for i in range(0, n_req, max(1, n_req // 8)):
-        g, K, bf = int(req_g[i]), int(req_K[i]), bool(req_bf[i])
-        C = np.empty((graphs[g]["m"], K), dtype=np.float32)
-        tk = sv.submit(gids[g], Bbuf[(g, K, bf)][1], C, ns.NS_BF16 if bf else ns.NS_F32)
-        while not sv.poll(tk)[0]:
-            time.sleep(0.0002)
-        ref = oracle.spmm(graphs[g], Bbuf[(g, K, bf)][1], b_bf16=bf, threads=threads)
-        errs.append((oracle.rel_frobenius(C, ref), bf))
+        clk.stop()
+    launches = ns.launch_count() - launches0
     sv.close()
-    pct = lambda a, q: float(np.percentile(a, q) * 1e3)
+
+    # ---- accuracy of the served results (sampled requests, sampled rows) vs the FP64 oracle ----
+    errs = {False: [], True: []}
+    for j, (r, Cr) in out_rows.items():
+        g, bf = int(req_g[j]), bool(req_bf[j])
+        ref = oracle.spmm(graphs[g], b_of(j), rows=r, b_bf16=bf, threads=threads)
+        errs[bf].append(oracle.rel_frobenius(Cr, ref))
+
+    # ---- the plain path: the first requests of the same trace, one at a time (plan + execute +
+    # copies through ns_spmm_host, as a caller without the server would do it) ----
+    n_plain = min(n_req, args.plain_requests)
+    lat_p = np.zeros(n_plain)
+    Cp, Cpv = pool.get(int(max(g["m"] for g in graphs)), 128)
+    tp = time.perf_counter()
+    for j in range(n_plain):
+        now = time.perf_counter() - tp
+        if arr[j] > now:
+            time.sleep(arr[j] - now)
+        g, K, bf = int(req_g[j]), int(req_K[j]), bool(req_bf[j])
+        ns.spmm_host(graphs[g], b_of(j), Cp.numpy()[:graphs[g]["m"] * K].reshape(-1, K),
+                     ns.NS_BF16 if bf else ns.NS_F32, tune)
+        lat_p[j] = time.perf_counter() - tp - arr[j]
+    wall_p = time.perf_counter() - tp
+    flops_p = float((2.0 * nnz[req_g[:n_plain]] * req_K[:n_plain]).sum())
+
+    pct = lambda a, q: float(np.percentile(a, q) * 1e3) if len(a) else None
+    worst = int(np.argmax(lat))
+    h2d = float(sum(graphs[int(g)]["n"] * int(K) * (2 if bf else 4) for g, K, bf in zip(req_g, req_K, req_bf)))
+    d2h = float(sum(graphs[int(g)]["m"] * int(K) * 4 for g, K in zip(req_g, req_K)))
+    all_err = errs[False] + errs[True]
     print(json.dumps({
-        "metric": "served SpMM throughput & p50/p99 latency", "value": flops / wall_s / 1e9,
-        "unit": "GFLOP/s", "n_gpus": 1, "higher_is_better": True, "dtype": "mixed f32/bf16",
-        "data": "synthetic",
+        "metric": "served SpMM throughput & p50/p99 latency", "value": flops / wall / 1e9,
+        "unit": "GFLOP/s", "n_gpus": 1, "steps": n_req, "warmup": len(graphs),
+        "ms_per_step": wall / n_req * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "mixed f32/bf16", "data": "synthetic",
         "config": {"workload": f"serve-poisson-{args.rate:g}/s-{args.duration:g}s-pool{args.pool}",
                    "requests": n_req, "K": "{32,64,128}", "b_dtype": "50/50 f32/bf16",
-                   "graph_nodes_median": float(np.median(sizes)), "graph_nodes_max": int(sizes.max())},
-        "served": {"requests_per_s": n_req / wall_s, "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99),
-                   "GFLOP_per_s": flops / wall_s / 1e9},
-        "plain": {"requests_per_s": n_req / wall_p, "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
-                  "GFLOP_per_s": flops / wall_p / 1e9, "how": "one request at a time, ns_spmm_host"},
-        "rel_frobenius_vs_fp64": max([e for e, b in errs] or [0.0]),
-        "accuracy": {"f32": max([e for e, b in errs if not b] or [0.0]),
-                     "bf16": max([e for e, b in errs if b] or [0.0]), "requests_checked": len(errs)}}))
+                   "graph_nodes_median": float(np.median(sizes)), "graph_nodes_max": int(sizes.max()),
+                   "pool_nnz": int(nnz.sum()), "max_inflight": args.inflight,
+                   "hbm_budget_gib": args.serve_budget, "tune": tune.as_dict(),
+                   "l2": "every request copies its B in and its C out (host buffers)"},
+        "served": {"requests_per_s": n_req / wall, "offered_per_s": args.rate,
+                   "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "max_ms": pct(lat, 100),
+                   "GFLOP_per_s": flops / wall / 1e9,
+                   "breakdown_p50_ms": {"admission_wait": pct(parts[:, 0], 50), "launch": pct(parts[:, 1], 50),
+                                        "device_and_copies": pct(parts[:, 2], 50)},
+                   "breakdown_p99_ms": {"admission_wait": pct(parts[:, 0], 99), "launch": pct(parts[:, 1], 99),
+                                        "device_and_copies": pct(parts[:, 2], 99)},
+                   "slowest_request": {"ms": lat[worst] * 1e3, "nodes": int(graphs[int(req_g[worst])]["n"]),
+                                       "K": int(req_K[worst]), "bf16": bool(req_bf[worst]),
+                                       "parts_ms": [float(x * 1e3) for x in parts[worst]]},
+                   "first_n_p50_ms": pct(lat[:n_plain], 50), "first_n_p99_ms": pct(lat[:n_plain], 99)},
+        "plain": {"requests": n_plain, "requests_per_s": n_plain / wall_p, "p50_ms": pct(lat_p, 50),
+                  "p99_ms": pct(lat_p, 99), "GFLOP_per_s": flops_p / wall_p / 1e9,
+                  "how": "the first requests of the trace, one at a time through ns_spmm_host"},
+        "planning": {"graphs": len(graphs), "warm_s": t_warm, "pool_generation_s": t_pool,
+                     "plan_ready_p50_s": float(np.median(plan_wait)) if plan_wait else None},
+        "rel_frobenius_vs_fp64": max(all_err) if all_err else None,
+        "accuracy": {"f32_max": max(errs[False]) if errs[False] else None,
+                     "bf16_max": max(errs[True]) if errs[True] else None,
+                     "requests_checked": len(all_err),
+                     "rows": "all rows of graphs up to 2048 nodes, else 2048 sampled rows"},
+        "e2e": {"value": flops / wall / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d / n_req,
+                "d2h_bytes_per_step": d2h / n_req},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }))
 
 
 if __name__ == "__main__":

@@ -113,6 +113,7 @@ typedef struct {
     int64_t n_split;  /* rows assembled from several pieces */
     int64_t n_slots;  /* partial-row slots */
     int64_t n_items;  /* work items of the execute launch */
+    int64_t device_bytes; /* device memory the plan holds */
 } ns_plan_stats_t;
 
 typedef struct ns_plan* ns_plan_t;
@@ -249,6 +250,16 @@ int32_t ns_rebalance_next(int32_t lo, int32_t hi, int32_t tau, double dt_tc, dou
 /* ---------------------------------------------------------------------------------------- */
 /* Serving: continuous batching of SpMM requests on one GPU.                                 */
 /* ---------------------------------------------------------------------------------------- */
+/* A server owns two host threads.  The planner builds the plan of each new (graph, K, dtype)
+ * key -- one plan per graph when the tune keeps every nonzero on the CUDA cores (tau_tile =
+ * NS_TAU_INF) and l2_hints != 2, since such a plan depends on neither K nor the dtype -- and
+ * plans stay resident for later requests.  The worker admits queued requests whose plan is
+ * built, in arrival order (a request waiting for its plan lets later ones pass), while slots are
+ * free and the request's device footprint (B, C, its plan's partial-row slots and counters) fits the budget
+ * beside the resident plans, evicting idle plans least recently used first.  With nothing in
+ * flight the oldest request is admitted even if plans of queued requests fill the budget, so the
+ * queue always moves.  Every request admitted since the last launch joins one persistent launch
+ * per (K, dtype, kernel) group; C is copied back on that launch's stream. */
 typedef struct ns_server* ns_server_t;
 
 typedef struct {
@@ -271,15 +282,21 @@ typedef struct {
 } ns_request_t;
 
 typedef struct {
-    double t_admit, t_start, t_done; /* seconds on the server clock (ns_serve_now) */
-    int32_t status;                  /* ns_status_t of the request                  */
+    double t_admit, t_start, t_done; /* seconds on the server clock (ns_serve_now): admitted,
+                                        launched, result in the host buffer                      */
+    int32_t status;                  /* ns_status_t of the request                               */
+    int32_t plan_built;              /* 1: this request was the first on its plan key (the plan
+                                        was built for it)                                         */
+    double t_planned;                /* when its plan became ready, if the request waited for it;
+                                        0 when the plan was already resident                      */
 } ns_req_stats_t;
 
 ns_status_t ns_serve_create(const ns_serve_cfg_t* cfg, ns_server_t* out);
 /* Register a host CSR graph; the server copies it.  Returns its id in *graph_id. */
 ns_status_t ns_serve_register_graph(ns_server_t sv, const ns_csr_t* A, int32_t* graph_id);
 /* Queue a request; returns immediately.  NS_ERR_AGAIN if the queue is full, NS_ERR_TOO_LARGE if
- * the request could never fit the HBM budget. */
+ * B + C + the plan estimate already exceed the HBM budget.  A request whose footprint with its
+ * built plan exceeds the budget fails later with NS_ERR_TOO_LARGE (reported by ns_serve_poll). */
 ns_status_t ns_serve_submit(ns_server_t sv, const ns_request_t* r, uint64_t* ticket);
 /* Non-blocking completion check; *done = 1 once C has been written to the host buffer. */
 ns_status_t ns_serve_poll(ns_server_t sv, uint64_t ticket, int* done, ns_req_stats_t* st);

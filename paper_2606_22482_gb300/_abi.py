@@ -41,7 +41,7 @@ class Tune(ctypes.Structure):
 class PlanStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in (
         "m", "n", "nnz", "K", "b_bf16", "TM", "TK", "m_aic", "n_win", "n_dtiles", "n_dwin",
-        "n_dvals", "n_res", "n_rl", "T", "n_chunks", "n_split", "n_slots", "n_items")]
+        "n_dvals", "n_res", "n_rl", "T", "n_chunks", "n_split", "n_slots", "n_items", "device_bytes")]
 
 
 class RebalanceReport(ctypes.Structure):
@@ -67,7 +67,8 @@ class Request(ctypes.Structure):
 
 class ReqStats(ctypes.Structure):
     _fields_ = [("t_admit", ctypes.c_double), ("t_start", ctypes.c_double),
-                ("t_done", ctypes.c_double), ("status", ctypes.c_int32)]
+                ("t_done", ctypes.c_double), ("status", ctypes.c_int32), ("plan_built", ctypes.c_int32),
+                ("t_planned", ctypes.c_double)]
 
 
 # every exported symbol of include/ns_spmm.h with (restype, argtypes)

@@ -198,6 +198,8 @@ ns_status_t plan_create(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, const 
         delete P;
         return r;
     }
+    P->st.device_bytes = 0;
+    for (auto& b : P->blocks) P->st.device_bytes += (int64_t)b.bytes;
     *out = P;
     return NS_OK;
 }

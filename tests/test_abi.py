@@ -99,3 +99,54 @@ def test_header_export_names_match_library_and_binding(ns):
     table = re.findall(r"^\s*A\((\w+),", api, re.M)
     assert listed == table
     assert tuple(listed) == tuple(ns.PLAN_ARRAYS)
+
+
+_CTYPE = {"int32_t": "c_int", "int64_t": "c_long", "double": "c_double", "ns_dtype_t": "c_int",
+          "ns_tune_t": "Tune"}
+
+
+def _header_structs():
+    """Field lists (name, C type) of every `typedef struct { ... } name;` in the header."""
+    src = open(os.path.join(ROOT, "include", "ns_spmm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", src, re.S):
+        fields = []
+        for decl in m.group(1).split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            tm = re.match(r"(const\s+)?([\w]+)\s*(\**)\s*(.*)$", decl)
+            ctype, ptr, rest = tm.group(2), tm.group(3), tm.group(4)
+            for name in rest.split(","):
+                name = name.strip()
+                p = ptr + ("*" * (len(name) - len(name.lstrip("*"))))
+                name = name.lstrip("*").strip()
+                arr = re.match(r"(\w+)\[(\d+)\]", name)
+                if arr:
+                    name = arr.group(1)
+                fields.append((name, "ptr" if p else ctype))
+        out[m.group(2)] = fields
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("ns_plan_stats_t", "PlanStats"), ("ns_req_stats_t", "ReqStats"),
+                                          ("ns_request_t", "Request"), ("ns_serve_cfg_t", "ServeCfg"),
+                                          ("ns_tune_t", "Tune")])
+def test_binding_structs_match_header(ns, cname, pyname):
+    # the ctypes mirrors of the header's structs: same fields, same order, same widths
+    import ctypes
+    hdr = _header_structs()[cname]
+    py = getattr(ns._abi, pyname)._fields_
+    assert [n for n, _ in hdr] == [n for n, _ in py], (cname, hdr, py)
+    for (n, ct), (_, pt) in zip(hdr, py):
+        if ct == "ptr":
+            assert ctypes.sizeof(pt) == ctypes.sizeof(ctypes.c_void_p), n
+        elif ct in ("int32_t", "ns_dtype_t"):
+            assert ctypes.sizeof(pt) == 4, n
+        elif ct == "int64_t":
+            assert ctypes.sizeof(pt) == 8, n
+        elif ct == "double":
+            assert pt is ctypes.c_double, n
+        elif ct == "ns_tune_t":
+            assert pt is ns._abi.Tune, n

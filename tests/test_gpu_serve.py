@@ -16,6 +16,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_2606_22482_gb300 as ns  # noqa: E402
+from nsutil import to_dev  # noqa: E402
 
 
 def pinned(shape, dtype):
@@ -76,6 +77,14 @@ def test_mix_matches_oracle_and_alone():
         assert st["t_done"] >= st["t_start"] >= st["t_admit"] > 0
         ref = oracle.spmm(graphs[g], B, b_bf16=bf16)
         assert oracle.rel_frobenius(C, ref) <= 1e-5
+    # the default tune keeps every nonzero on the CUDA cores: one plan per graph serves every K
+    # and dtype, built for the first request on the graph
+    firsts = {}
+    for k, (g, K, bf16, B) in enumerate(reqs):
+        firsts.setdefault(g, k)
+    assert [k for k, st in enumerate(stats) if st["plan_built"]] == sorted(firsts.values())
+    for k in firsts.values():
+        assert stats[k]["t_planned"] > 0 and stats[k]["t_admit"] >= stats[k]["t_planned"]
     # the same requests one at a time
     for i in (0, 7, 13, 29):
         alone, _ = serve(graphs, [reqs[i]], max_inflight=1)
@@ -108,3 +117,62 @@ def test_small_budget_still_serves_everything():
     outs, stats = serve(graphs, reqs, hbm_budget_bytes=int(need * 2.5), max_inflight=8)
     for (g, K, bf16, B), C in zip(reqs, outs):
         assert oracle.rel_frobenius(C, oracle.spmm(graphs[0], B)) <= 1e-5
+
+
+def test_hybrid_tune_plans_per_key():
+    # with dense tiles the plan depends on K and dtype: one plan per (graph, K, dtype)
+    graphs = [synth.block_sparse_csr(2048, seed=4, block=16, band=2, p_random=0.05),
+              synth.serve_graph(3000, seed=2)]
+    reqs = make_requests(graphs, 24, seed=5)
+    tune = ns.tune_default()
+    tune.tau_tile, tune.TM = 48, 16
+    outs, stats = serve(graphs, reqs, max_inflight=8, tune=tune)
+    keys = {}
+    for k, (g, K, bf16, B) in enumerate(reqs):
+        keys.setdefault((g, K, bf16), k)
+    assert [k for k, st in enumerate(stats) if st["plan_built"]] == sorted(keys.values())
+    for (g, K, bf16, B), C, st in zip(reqs, outs, stats):
+        assert st["status"] == 0
+        ref = oracle.spmm(graphs[g], B, b_bf16=bf16)
+        assert oracle.rel_frobenius(C, ref) <= (2e-2 if bf16 else 1e-5)
+
+
+def _al256(b):
+    return (b + 255) // 256 * 256
+
+
+def test_admission_by_built_plan_size():
+    # a budget that the submit-time estimate fits but the built plan plus the request's slots do
+    # not: the request is refused at admission with NS_ERR_TOO_LARGE (7), and the server goes on
+    g = synth.serve_graph(30000, seed=9)
+    K = 128
+    At = to_dev(g, torch.device("cuda", 0))
+    with ns.spmm_plan(At, K, ns.NS_F32) as p:
+        st = p.stats()
+    est = g["m"] * 24 + g.nnz * 8 + 4096
+    io = _al256(g["n"] * K * 4) + _al256(g["m"] * K * 4)
+    submit_need = io + _al256(4) + est                        # no slots, one counter word
+    admit_need = io + _al256(st["n_slots"] * K * 4) + _al256(max(st["n_split"], 1) * 4) + st["device_bytes"]
+    if admit_need <= submit_need:
+        pytest.skip("the estimate covers this plan")
+    B = pinned((g["n"], K), torch.float32)
+    B[...] = synth.dense_b(g["n"], K, seed=1)
+    C = pinned((g["m"], K), torch.float32)
+    sv = ns.Server(hbm_budget_bytes=submit_need, max_inflight=2)
+    gid = sv.register(g)
+    t = sv.submit(gid, B, C)
+    t0 = time.time()
+    while True:
+        try:
+            done, _ = sv.poll(t)
+        except ns.NsError as e:
+            assert e.code == 7
+            break
+        assert not done, "admitted over the budget"
+        assert time.time() - t0 < 30
+        time.sleep(0.001)
+    # a budget with room for the built plan serves the same request
+    sv.close()
+    outs, stats = serve([g], [(0, K, False, np.asarray(B))], hbm_budget_bytes=admit_need, max_inflight=2)
+    assert stats[0]["status"] == 0
+    assert oracle.rel_frobenius(outs[0], oracle.spmm(g, np.asarray(B))) <= 1e-5

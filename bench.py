@@ -133,12 +133,10 @@ class ClockSampler:
 # from one ncu capture (summarised in profiles/), keyed by workload and tune.  It is valid only for
 # the kernel source it was taken on: the digest of the execute kernel's sources must match,
 # otherwise the roofline reports traffic as null.
-EXEC_SOURCES = ("ns_exec.cu", "ns_internal.cuh", "ns_dense.cuh", "ns_ptx.cuh")
+EXEC_SOURCES = ("ns_exec.cu", "ns_internal.cuh", "ns_dense.cuh", "ns_dense_tc.cuh", "ns_ptx.cuh")
 MEASURED_TRAFFIC = {
     # (workload, tau_tile, chunk_nnz, l2_hints): (source digest, bytes per launch)
-    ("powerlaw", 2147483647, 512, 1): ("92ae39a35c43ac30", 1676669184 + 541900032),
-    ("powerlaw", 2147483647, 256, 1): ("92ae39a35c43ac30", 1698748416 + 586447872),
-    ("powerlaw", 2147483647, 1024, 1): ("92ae39a35c43ac30", 1671091712 + 530661120),
+    ("powerlaw", 2147483647, 512, 1): ("7225b1265f753280", 1676309000 + 542861312),
 }
 
 
@@ -315,6 +313,7 @@ def main():
     ap.add_argument("--serve-budget", type=float, default=64.0, help="serve: HBM budget (GiB)")
     ap.add_argument("--plain-requests", type=int, default=2000,
                     help="serve: requests of the trace also run one at a time (plain path)")
+    ap.add_argument("--serve-trace", default=None, help="serve: write per-request times to this .npz")
     ap.add_argument("--serve-checks", type=int, default=400,
                     help="serve: about this many served results compared with the oracle")
     ap.add_argument("--tau", default="auto", help="'auto' (autotuner), 'inf' or an integer")
@@ -731,9 +730,18 @@ class PinnedPool:
         self.torch = torch
         self.free = {}
 
+    @staticmethod
+    def size_class(n: int) -> int:
+        return 1 << (max(1, n) - 1).bit_length()
+
+    def prewarm(self, cls: int, count: int) -> None:
+        lst = self.free.setdefault(cls, [])
+        while len(lst) < count:
+            lst.append(self.torch.empty(cls, dtype=self.torch.float32).pin_memory())
+
     def get(self, m: int, K: int):
         n = max(1, m * K)
-        cls = 1 << (n - 1).bit_length()
+        cls = self.size_class(n)
         lst = self.free.setdefault(cls, [])
         t = lst.pop() if lst else self.torch.empty(cls, dtype=self.torch.float32).pin_memory()
         return t, t.numpy()[:m * K].reshape(m, K)
@@ -780,17 +788,28 @@ def bench_serve(args, threads):
         return np.sort(np.random.default_rng(i).choice(m, 2048, replace=False)).astype(np.int32)
 
     pool = PinnedPool()
+    # result buffers of about 50 ms of arrivals per size class, page-locked before the trace
+    # (pinning memory takes driver locks that would stall the server's threads mid-trace)
+    cls_of = np.array([PinnedPool.size_class(graphs[int(g)]["m"] * int(K)) for g, K in zip(req_g, req_K)])
+    budget = 24 << 30
+    for c in sorted(set(cls_of.tolist())):
+        cnt = int((cls_of == c).sum())
+        want = min(cnt, max(2, int(np.ceil(args.rate * 0.05 * cnt / n_req))))
+        want = min(want, max(1, budget // (4 * c)))
+        budget -= want * 4 * c
+        pool.prewarm(c, want)
     tune = ns.tune_default()
     sv = ns.Server(hbm_budget_bytes=int(args.serve_budget * (1 << 30)), max_inflight=args.inflight,
                    max_queue=1 << 16, max_graphs=len(graphs) + 16, tune=tune)
     gids = [sv.register(g) for g in graphs]
     # warm: the planner builds every graph's plan once (one plan per graph serves every K and
-    # dtype under this tune); plans stay resident for the trace
+    # dtype under this tune) and the widest requests (K = 128, FP32) fill the server's device
+    # block cache; plans stay resident for the trace
     t_w = ns.now()
     warm = {}
     for g in range(len(graphs)):
-        Ct, Cv = pool.get(graphs[g]["m"], 32)
-        warm[sv.submit(gids[g], Bf32_np[:graphs[g]["n"] * 32].reshape(-1, 32), Cv, ns.NS_F32)] = Ct
+        Ct, Cv = pool.get(graphs[g]["m"], 128)
+        warm[sv.submit(gids[g], Bf32_np[:graphs[g]["n"] * 128].reshape(-1, 128), Cv, ns.NS_F32)] = Ct
     plan_wait = []
     while warm:
         for tk in list(warm):
@@ -804,7 +823,9 @@ def bench_serve(args, threads):
 
     # ---- the timed trace ----
     lat = np.zeros(n_req)
-    parts = np.zeros((n_req, 3))                # admission wait, launch, device + copies
+    # admission wait, launch, device + copies (host view); then the device part on the GPU's clock:
+    # B uploaded, kernel done, C copied, completion seen by the server
+    parts = np.zeros((n_req, 7))
     out_rows = {}
     pending = {}
     launches0 = ns.launch_count()
@@ -826,7 +847,9 @@ def bench_serve(args, threads):
                     j, Ct, Cv = pending.pop(tk)
                     ta = t0 + arr[j]
                     lat[j] = st["t_done"] - ta
-                    parts[j] = (st["t_admit"] - ta, st["t_start"] - st["t_admit"], st["t_done"] - st["t_start"])
+                    parts[j] = (st["t_admit"] - ta, st["t_start"] - st["t_admit"], st["t_done"] - st["t_start"],
+                                st["t_h2d"] - st["t_start"], st["t_exec"] - st["t_h2d"], st["t_d2h"] - st["t_exec"],
+                                st["t_done"] - st["t_d2h"])
                     if j % check_every == 0:
                         r = rows_to_check(j)
                         out_rows[j] = (r, Cv[r].copy())
@@ -836,6 +859,9 @@ def bench_serve(args, threads):
         clk.stop()
     launches = ns.launch_count() - launches0
     sv.close()
+    if args.serve_trace:
+        np.savez(args.serve_trace, arrival=arr, lat=lat, parts=parts, g=req_g, K=req_K, bf16=req_bf,
+                 nodes=np.array([graphs[int(g)]["n"] for g in req_g]))
 
     # ---- accuracy of the served results (sampled requests, sampled rows) vs the FP64 oracle ----
     errs = {False: [], True: []}
@@ -863,6 +889,13 @@ def bench_serve(args, threads):
 
     pct = lambda a, q: float(np.percentile(a, q) * 1e3) if len(a) else None
     worst = int(np.argmax(lat))
+    # size classes as the server forms them: B + C above 32 MB is a bulk request
+    io = np.array([graphs[int(g)]["n"] * int(K) * (2 if bf else 4) + graphs[int(g)]["m"] * int(K) * 4
+                   for g, K, bf in zip(req_g, req_K, req_bf)], dtype=np.int64)
+    bulk = io > (32 << 20)
+    by_class = {name: {"share": float(sel.mean()), "p50_ms": pct(lat[sel], 50), "p99_ms": pct(lat[sel], 99),
+                       "device_and_copies_p99_ms": pct(parts[sel, 2], 99)}
+                for name, sel in (("small", ~bulk), ("bulk", bulk))}
     h2d = float(sum(graphs[int(g)]["n"] * int(K) * (2 if bf else 4) for g, K, bf in zip(req_g, req_K, req_bf)))
     d2h = float(sum(graphs[int(g)]["m"] * int(K) * 4 for g, K in zip(req_g, req_K)))
     all_err = errs[False] + errs[True]
@@ -884,10 +917,15 @@ def bench_serve(args, threads):
                                         "device_and_copies": pct(parts[:, 2], 50)},
                    "breakdown_p99_ms": {"admission_wait": pct(parts[:, 0], 99), "launch": pct(parts[:, 1], 99),
                                         "device_and_copies": pct(parts[:, 2], 99)},
+                   "device_breakdown_p99_ms": {"h2d_after_launch": pct(parts[:, 3], 99), "execute": pct(parts[:, 4], 99),
+                                               "d2h": pct(parts[:, 5], 99), "seen_by_server": pct(parts[:, 6], 99)},
                    "slowest_request": {"ms": lat[worst] * 1e3, "nodes": int(graphs[int(req_g[worst])]["n"]),
                                        "K": int(req_K[worst]), "bf16": bool(req_bf[worst]),
-                                       "parts_ms": [float(x * 1e3) for x in parts[worst]]},
-                   "first_n_p50_ms": pct(lat[:n_plain], 50), "first_n_p99_ms": pct(lat[:n_plain], 99)},
+                                       "parts_ms": dict(zip(["admission_wait", "launch", "device_and_copies",
+                                                             "h2d_after_launch", "execute", "d2h", "seen_by_server"],
+                                                            [float(x * 1e3) for x in parts[worst]]))},
+                   "first_n_p50_ms": pct(lat[:n_plain], 50), "first_n_p99_ms": pct(lat[:n_plain], 99),
+                   "by_size_class": by_class},
         "plain": {"requests": n_plain, "requests_per_s": n_plain / wall_p, "p50_ms": pct(lat_p, 50),
                   "p99_ms": pct(lat_p, 99), "GFLOP_per_s": flops_p / wall_p / 1e9,
                   "how": "the first requests of the trace, one at a time through ns_spmm_host"},

@@ -289,6 +289,8 @@ typedef struct {
                                         was built for it)                                         */
     double t_planned;                /* when its plan became ready, if the request waited for it;
                                         0 when the plan was already resident                      */
+    double t_h2d, t_exec, t_d2h;     /* on the GPU, mapped to the server clock: its launch's B
+                                        uploads done, its launch's kernel done, its C copy done   */
 } ns_req_stats_t;
 
 ns_status_t ns_serve_create(const ns_serve_cfg_t* cfg, ns_server_t* out);
@@ -335,6 +337,20 @@ const char* ns_last_error(void);
 int64_t ns_launch_count(void);
 /* 1 if the library was built for the device it runs on (sm_103a), else 0. */
 int32_t ns_device_ok(void);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Fault injection on the host (tests; no counterpart in the paper).  Neither faults a GPU:   */
+/* they drive the library's error paths the way a failing call or a kernel guard would.      */
+/* ---------------------------------------------------------------------------------------- */
+/* After `after` more successful device allocations by the library (plans, scratch, served
+ * requests), the next one fails as if the device were out of memory, once; after = -1 turns the
+ * injection off.  Process-wide. */
+ns_status_t ns_inject_alloc_failure(int32_t after);
+/* OR `bits` (NS status bits: 2 = a bounded wait gave up, 4 = an index out of range) into the
+ * plan's device status word, as a kernel guard would.  Synchronous.  The plan's next execute
+ * copies the word back and the execute after it returns NS_ERR_TIMEOUT (bit 2) or NS_ERR_CUDA.
+ * Errors: NS_ERR_INVALID (NULL plan, bits outside 2 | 4), NS_ERR_CUDA. */
+ns_status_t ns_plan_inject_status(ns_plan_t p, int32_t bits);
 
 #ifdef __cplusplus
 }

@@ -94,6 +94,10 @@ class Plan:
                                  out.nbytes))
         return out
 
+    def inject_status(self, bits: int) -> None:
+        """ns_plan_inject_status: OR status bits (2 timeout, 4 bad index) into the device word."""
+        check(lib.ns_plan_inject_status(self._h, int(bits)))
+
     def execute(self, B, C, stream=None) -> None:
         """C := A @ B on the device (B: n x K float32 or bfloat16 tensor, C: m x K float32)."""
         spmm_execute(self, B, C, stream)
@@ -154,6 +158,11 @@ def spmm_host(A: dict, B: np.ndarray, C: np.ndarray, b_dtype: int = NS_F32,
                            ctypes.c_void_p(C.ctypes.data),
                            ctypes.byref(tune) if tune is not None else None,
                            _stream_handle(stream)))
+
+
+def inject_alloc_failure(after: int) -> None:
+    """ns_inject_alloc_failure: the allocation after `after` more successful ones fails (-1: off)."""
+    check(lib.ns_inject_alloc_failure(int(after)))
 
 
 def launch_count() -> int:

@@ -68,7 +68,8 @@ class Request(ctypes.Structure):
 class ReqStats(ctypes.Structure):
     _fields_ = [("t_admit", ctypes.c_double), ("t_start", ctypes.c_double),
                 ("t_done", ctypes.c_double), ("status", ctypes.c_int32), ("plan_built", ctypes.c_int32),
-                ("t_planned", ctypes.c_double)]
+                ("t_planned", ctypes.c_double), ("t_h2d", ctypes.c_double), ("t_exec", ctypes.c_double),
+                ("t_d2h", ctypes.c_double)]
 
 
 # every exported symbol of include/ns_spmm.h with (restype, argtypes)
@@ -110,6 +111,8 @@ SIGNATURES = {
     "ns_last_error": (ctypes.c_char_p, []),
     "ns_launch_count": (I64, []),
     "ns_device_ok": (I32, []),
+    "ns_inject_alloc_failure": (ctypes.c_int, [I32]),
+    "ns_plan_inject_status": (ctypes.c_int, [P, I32]),
 }
 
 

@@ -1,4 +1,5 @@
 // ns_api.cu -- the C ABI (include/ns_spmm.h): argument checks, plan lifetime, export, execute.
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -44,8 +45,20 @@ static cudaMemPool_t pool_for(int dev)
     return g_pool[dev];
 }
 
+static std::mutex g_inject_mu;
+static int32_t g_alloc_countdown = -1;  // injection: allocations to pass before one fails
+
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s)
 {
+    {
+        std::lock_guard<std::mutex> lk(g_inject_mu);
+        if (g_alloc_countdown == 0) {
+            g_alloc_countdown = -1;
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+        if (g_alloc_countdown > 0) --g_alloc_countdown;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -232,6 +245,32 @@ void ns_tune_default(ns_tune_t* t)
 const char* ns_last_error(void) { return t_err.c_str(); }
 
 int64_t ns_launch_count(void) { return g_launches.load(); }
+
+ns_status_t ns_inject_alloc_failure(int32_t after)
+{
+    if (after < -1) {
+        set_error("after must be >= -1");
+        return NS_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    g_alloc_countdown = after;
+    return NS_OK;
+}
+
+ns_status_t ns_plan_inject_status(ns_plan_t p, int32_t bits)
+{
+    Plan* P = reinterpret_cast<Plan*>(p);
+    if (!P || bits == 0 || (bits & ~(kStatusTimeout | kStatusInternal))) {
+        set_error("NULL plan or status bits outside 2 | 4");
+        return NS_ERR_INVALID;
+    }
+    int32_t cur = 0;
+    NS_CUDA_TRY(cudaStreamSynchronize(P->last_stream));
+    NS_CUDA_TRY(cudaMemcpy(&cur, P->ctrl + 2, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    cur |= bits;
+    NS_CUDA_TRY(cudaMemcpy(P->ctrl + 2, &cur, sizeof(int32_t), cudaMemcpyHostToDevice));
+    return NS_OK;
+}
 
 int32_t ns_device_ok(void)
 {

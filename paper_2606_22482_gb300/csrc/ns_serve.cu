@@ -11,14 +11,20 @@
 //                     free and their footprint (B + C + the plan's own partial-row slots) fits
 //                     the HBM budget beside the resident plans; idle plans are evicted, least
 //                     recently used first, to make room;
-//            prepare: B is copied to the device on the copy stream;
 //            launch : every request admitted since the last launch joins ONE persistent launch
-//                     per (K, dtype, kernel) group: their work lists are merged by cost class and
-//                     each item carries its request's descriptor (staged through pinned host
-//                     memory, so the upload never waits for running launches); launches
-//                     alternate between two streams so a new batch overlaps the running ones;
-//            retire : when a launch's event completes, its requests are done (C was copied back
-//                     on the launch's stream) and their memory returns to the budget.
+//                     per (size class, K, dtype, kernel) group: their B go up on the class's copy
+//                     stream, their work lists are merged by cost class and each item carries its
+//                     request's descriptor (staged through pinned host memory, so the upload never
+//                     waits for running launches); the C copies follow the kernel, smallest
+//                     first, each with its own event.  Requests whose B + C exceed 32 MB form the
+//                     bulk class, with its own copy and execute streams, so small requests never
+//                     queue behind a bulk request's copies; within a class launches alternate
+//                     between two streams so a new batch overlaps the running ones;
+//            retire : a request is done when its C copy's event completes; its memory returns
+//                     to the budget and its device block to the server's block cache.
+// Device blocks (a request's B, C and scratch; a launch's descriptors and work list) come from a
+// cache of blocks whose last use the worker has seen complete, in power-of-two sizes, so reusing
+// one never makes a stream wait for another's work and the steady state allocates nothing.
 // Requests never share execution scratch (each owns its partial-row slots and their counters),
 // so two requests on the same plan may run in the same or in overlapping launches.
 #include <algorithm>
@@ -76,10 +82,13 @@ struct SReq {
     int64_t bytes = 0;
     SPlan* sp = nullptr;
     void* block = nullptr;  // B, C, the partial-row slots and their counters on the device
+    size_t block_bytes = 0; // its size class
     void* dB = nullptr;
     float* dC = nullptr;
     float* slots = nullptr;
     int32_t* cnt = nullptr;
+    int cls = 0;                    // size class: 1 = bulk
+    cudaEvent_t done_ev = nullptr;  // recorded after the copy of C to the host
 };
 
 struct Pinned {
@@ -88,12 +97,33 @@ struct Pinned {
 };
 
 struct SLaunch {
-    std::vector<SReq*> reqs;
-    void* block = nullptr;  // descriptors, work list, ctrl (device)
-    Pinned staging;         // the same, host side
-    cudaEvent_t ev = nullptr;
-    cudaStream_t stream = nullptr;
+    std::vector<SReq*> reqs;      // requests not retired yet
+    cudaEvent_t h2d_ev = nullptr;   // the group's B uploads done (timing)
+    cudaEvent_t exec_ev = nullptr;  // its kernel done (timing)
+    Pinned staging;               // descriptors, work list and ctrl, host side
+    cudaEvent_t up_ev = nullptr;  // their upload has finished: the staging may be reused
+    void* block = nullptr;        // the same on the device (back to the cache with the last request)
+    size_t block_bytes = 0;
 };
+
+constexpr int64_t kBulkBytes = 32ll << 20;  // B + C above this: the bulk size class
+// Bulk requests admitted at once.  The copy engines take copies in arrival order whatever their
+// stream, so bulk transfers queued ahead of a small request's copies delay it by their whole
+// length; with at most this many bulk requests in flight that delay stays a few milliseconds,
+// and bulk requests wait in the queue instead (small ones pass them).
+constexpr int kBulkInflight = 2;
+
+// Host<->device copies go in pieces of at most 4 MB: a copy engine switches between streams at
+// copy boundaries, so a small request's copy waits at most one piece behind a bulk transfer.
+constexpr size_t kCopyPiece = 4u << 20;
+
+static void copy_pieces(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s)
+{
+    for (size_t off = 0; off < bytes; off += kCopyPiece) {
+        const size_t len = bytes - off < kCopyPiece ? bytes - off : kCopyPiece;
+        cudaMemcpyAsync(static_cast<char*>(dst) + off, static_cast<const char*>(src) + off, len, kind, s);
+    }
+}
 
 struct Server {
     ns_serve_cfg_t cfg{};
@@ -110,11 +140,19 @@ struct Server {
     std::map<uint64_t, SPlan> plans;
     uint64_t next_ticket = 1;
     int inflight = 0;
+    int bulk_inflight = 0;
     int64_t used = 0;
-    cudaStream_t s_plan = nullptr, s_copy = nullptr, s_exec[2] = {nullptr, nullptr};
-    int flip = 0;
+    cudaStream_t s_plan = nullptr, s_copy[2] = {nullptr, nullptr};
+    cudaStream_t s_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [size class][alternate]
+    int flip[2] = {0, 0};
     std::list<SLaunch> launches;
     std::vector<Pinned> pinned_free;  // staging buffers ready for reuse (worker thread only)
+    std::multimap<size_t, void*> dev_free;  // device blocks whose last use has completed (worker)
+    cudaEvent_t ref_ev = nullptr;  // GPU time origin: completed at server clock t_ref
+    void* zeros = nullptr;         // pinned zeros: split counters are cleared by a copy, not a kernel
+    size_t zeros_bytes = 0;
+    double t_ref = 0;
+    size_t dev_cached = 0;
 };
 
 static bool plan_per_graph(const ns_tune_t& t) { return t.tau_tile == kTauInf && t.l2_hints != 2; }
@@ -193,6 +231,7 @@ static void finish_req(Server* S, SReq* q, ns_status_t code)
     if (q->state >= 1) {
         S->inflight--;
         S->used -= q->bytes;
+        if (q->cls) S->bulk_inflight--;
     }
     q->state = 3;
     release_plan(S, q->sp);
@@ -277,6 +316,12 @@ static void admit(Server* S, std::vector<SReq*>& fresh)
             continue;
         }
         const SGraph& g = S->graphs[q->r.graph_id];
+        const size_t eb = q->r.b_dtype == NS_BF16 ? 2 : 4;
+        const int cls = (int64_t)(al256((size_t)g.n * q->r.K * eb) + al256((size_t)g.m * q->r.K * 4)) > kBulkBytes;
+        if (cls && S->bulk_inflight >= kBulkInflight) {  // small requests behind it may pass
+            ++it;
+            continue;
+        }
         const int64_t need = req_bytes(g, q->r.K, q->r.b_dtype, sp->plan->st.n_slots, sp->plan->st.n_split);
         if (need + sp->bytes > S->cfg.hbm_budget_bytes) {
             it = S->queue.erase(it);
@@ -290,6 +335,8 @@ static void admit(Server* S, std::vector<SReq*>& fresh)
         it = S->queue.erase(it);
         const double now = serve_clock();
         q->bytes = need;
+        q->cls = cls;
+        S->bulk_inflight += cls;
         S->used += need;
         sp->last_used = now;
         q->state = 1;
@@ -298,6 +345,54 @@ static void admit(Server* S, std::vector<SReq*>& fresh)
         S->inflight++;
         fresh.push_back(q);
     }
+}
+
+static size_t block_class(size_t bytes)
+{
+    size_t c = 64 << 10;
+    while (c < bytes) c <<= 1;
+    return c;
+}
+
+// a device block of at least `bytes` (its size class in *cls): the smallest cached block of that
+// class or up to three classes larger, else a new one from the pool.  Growing the pool maps new
+// memory, which holds the worker for milliseconds, so a larger idle block is the better choice.
+static void* get_block(Server* S, size_t bytes, size_t* cls, cudaStream_t s)
+{
+    *cls = block_class(bytes);
+    auto it = S->dev_free.lower_bound(*cls);
+    if (it != S->dev_free.end() && it->first <= 8 * *cls) {
+        void* p = it->second;
+        *cls = it->first;
+        S->dev_free.erase(it);
+        S->dev_cached -= *cls;
+        return p;
+    }
+    void* p = nullptr;
+    if (pool_alloc(&p, *cls, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        // make room from the cache and try once more
+        for (auto& kv : S->dev_free) cudaFreeAsync(kv.second, s);
+        S->dev_free.clear();
+        S->dev_cached = 0;
+        if (pool_alloc(&p, *cls, s) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+    }
+    return p;
+}
+
+// a block whose last use has completed goes back to the cache (at most half the budget is kept)
+static void put_block(Server* S, void* p, size_t cls)
+{
+    if (!p) return;
+    if ((int64_t)(S->dev_cached + cls) > S->cfg.hbm_budget_bytes / 2) {
+        cudaFreeAsync(p, S->s_copy[0]);
+        return;
+    }
+    S->dev_free.emplace(cls, p);
+    S->dev_cached += cls;
 }
 
 static Pinned get_pinned(Server* S, size_t bytes)
@@ -319,7 +414,7 @@ static Pinned get_pinned(Server* S, size_t bytes)
     return p;
 }
 
-// device memory of the fresh requests and the upload of their B
+// device memory of the fresh requests
 static void prepare(Server* S, std::vector<SReq*>& fresh, std::vector<SReq*>& ready)
 {
     for (SReq* q : fresh) {
@@ -330,9 +425,8 @@ static void prepare(Server* S, std::vector<SReq*>& fresh, std::vector<SReq*>& re
         const size_t bC = al256((size_t)g.m * q->r.K * 4);
         const size_t bS = al256((size_t)P->st.n_slots * q->r.K * 4);
         const size_t bN = al256((size_t)(P->st.n_split > 0 ? P->st.n_split : 1) * 4);
-        void* blk = nullptr;
-        if (pool_alloc(&blk, bB + bC + bS + bN, S->s_copy) != cudaSuccess) {
-            (void)cudaGetLastError();
+        void* blk = get_block(S, bB + bC + bS + bN, &q->block_bytes, S->s_copy[q->cls]);
+        if (!blk) {
             std::lock_guard<std::mutex> lk(S->mu);
             finish_req(S, q, NS_ERR_OOM);
             continue;
@@ -342,15 +436,16 @@ static void prepare(Server* S, std::vector<SReq*>& fresh, std::vector<SReq*>& re
         q->dC = reinterpret_cast<float*>(static_cast<char*>(blk) + bB);
         q->slots = reinterpret_cast<float*>(static_cast<char*>(blk) + bB + bC);
         q->cnt = reinterpret_cast<int32_t*>(static_cast<char*>(blk) + bB + bC + bS);
-        cudaMemsetAsync(q->cnt, 0, bN, S->s_copy);  // split-row arrival counters start at zero
-        if (g.n > 0) cudaMemcpyAsync(q->dB, q->r.B, (size_t)g.n * q->r.K * eb, cudaMemcpyHostToDevice, S->s_copy);
+        // split-row arrival counters start at zero: a copy from pinned zeros keeps the copy stream
+        // off the SMs (a memset is a kernel, which would wait behind running SpMM launches)
+        if (bN <= S->zeros_bytes) cudaMemcpyAsync(q->cnt, S->zeros, bN, cudaMemcpyHostToDevice, S->s_copy[q->cls]);
+        else cudaMemsetAsync(q->cnt, 0, bN, S->s_copy[q->cls]);
         ready.push_back(q);
     }
 }
 
-// one persistent launch for a group of requests sharing K, dtype and kernel
-static void launch_group(Server* S, std::vector<SReq*>& rs, int K, bool bf16, bool dense, int TM, int TK,
-                         cudaEvent_t copied)
+// one persistent launch for a group of requests sharing size class, K, dtype and kernel
+static void launch_group(Server* S, std::vector<SReq*>& rs, int cls, int K, bool bf16, bool dense, int TM, int TK)
 {
     struct It {
         int cls;
@@ -375,25 +470,35 @@ static void launch_group(Server* S, std::vector<SReq*>& rs, int K, bool bf16, bo
         return a.rank < b.rank;
     });
     const int64_t ni = (int64_t)items.size();
-    SLaunch L;
-    L.reqs = rs;
-    L.stream = S->s_exec[S->flip];
-    S->flip ^= 1;
+    cudaStream_t cs = S->s_copy[cls];
+    cudaStream_t es = S->s_exec[cls][S->flip[cls]];
+    S->flip[cls] ^= 1;
     const size_t bD = al256(descs.size() * sizeof(ExecDesc));
     const size_t bQ = al256((size_t)(ni > 0 ? ni : 1) * 4);
     const size_t total = bD + 2 * bQ + 256;
+    SLaunch L;
     L.staging = get_pinned(S, total);
-    if (!L.staging.p || pool_alloc(&L.block, total, L.stream) != cudaSuccess) {
-        (void)cudaGetLastError();
+    void* block = L.staging.p ? get_block(S, total, &L.block_bytes, es) : nullptr;
+    if (!block) {
         if (L.staging.p) S->pinned_free.push_back(L.staging);
+        cudaStreamSynchronize(cs);  // the counters' memsets: then the blocks are idle
         std::lock_guard<std::mutex> lk(S->mu);
         for (SReq* q : rs) {
-            cudaFreeAsync(q->block, S->s_copy);
+            put_block(S, q->block, q->block_bytes);
             q->block = nullptr;
             finish_req(S, q, NS_ERR_OOM);
         }
         return;
     }
+    L.block = block;
+    // B of every request on the class's copy stream
+    for (SReq* q : rs) {
+        const SGraph& g = S->graphs[q->r.graph_id];
+        const size_t eb = q->r.b_dtype == NS_BF16 ? 2 : 4;
+        if (g.n > 0) copy_pieces(q->dB, q->r.B, (size_t)g.n * q->r.K * eb, cudaMemcpyHostToDevice, cs);
+    }
+    cudaEventCreate(&L.h2d_ev);
+    cudaEventRecord(L.h2d_ev, cs);
     char* h = static_cast<char*>(L.staging.p);
     std::memcpy(h, descs.data(), descs.size() * sizeof(ExecDesc));
     int32_t* hq = reinterpret_cast<int32_t*>(h + bD);
@@ -403,38 +508,112 @@ static void launch_group(Server* S, std::vector<SReq*>& rs, int K, bool bf16, bo
         hd[j] = items[j].slot;
     }
     std::memset(h + bD + 2 * bQ, 0, 256);  // ctrl: work ticket and status
-    char* base = static_cast<char*>(L.block);
-    cudaStreamWaitEvent(L.stream, copied, 0);
-    cudaMemcpyAsync(base, h, total, cudaMemcpyHostToDevice, L.stream);
+    char* base = static_cast<char*>(block);
+    cudaMemcpyAsync(base, h, total, cudaMemcpyHostToDevice, es);
+    cudaEventCreateWithFlags(&L.up_ev, cudaEventDisableTiming);
+    cudaEventRecord(L.up_ev, es);
+    cudaStreamWaitEvent(es, L.h2d_ev, 0);
+    // a bulk launch leaves a quarter of the GPU free, so small requests' launches start at once
     int grid = 0;
+    if (cls) {
+        const int contig = 0;
+        if (exec_prepare(ni, K, TM, TK, bf16, S->cfg.tune.l2_hints != 0, dense, &grid, S->cfg.tune.chunk_nnz,
+                         contig) != NS_OK)
+            grid = 0;
+        grid = grid > 4 ? grid * 3 / 4 : grid;
+    }
     ns_status_t r = exec_launch(reinterpret_cast<ExecDesc*>(base), reinterpret_cast<int32_t*>(base + bD),
                                 reinterpret_cast<int32_t*>(base + bD + bQ), ni,
                                 reinterpret_cast<int32_t*>(base + bD + 2 * bQ), K, TM, TK, bf16,
-                                S->cfg.tune.l2_hints != 0, dense, &grid, L.stream, nullptr,
-                                S->cfg.tune.chunk_nnz);
+                                S->cfg.tune.l2_hints != 0, dense, &grid, es, nullptr, S->cfg.tune.chunk_nnz);
+    cudaEventCreate(&L.exec_ev);
+    cudaEventRecord(L.exec_ev, es);
     const double t_start = serve_clock();
-    for (SReq* q : rs) {
+    // C back to the host, smallest first; each request's event follows its copy
+    std::vector<SReq*> order(rs);
+    std::stable_sort(order.begin(), order.end(), [&](const SReq* a, const SReq* b) {
+        return (int64_t)S->graphs[a->r.graph_id].m * a->r.K < (int64_t)S->graphs[b->r.graph_id].m * b->r.K;
+    });
+    for (SReq* q : order) {
         const SGraph& g = S->graphs[q->r.graph_id];
         q->st.t_start = t_start;
-        if (g.m > 0) cudaMemcpyAsync(q->r.C, q->dC, (size_t)g.m * q->r.K * 4, cudaMemcpyDeviceToHost, L.stream);
+        if (r == NS_OK && g.m > 0)
+            copy_pieces(q->r.C, q->dC, (size_t)g.m * q->r.K * 4, cudaMemcpyDeviceToHost, es);
+        cudaEventCreate(&q->done_ev);
+        cudaEventRecord(q->done_ev, es);
     }
-    cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming);
-    cudaEventRecord(L.ev, L.stream);
     std::lock_guard<std::mutex> lk(S->mu);
     if (r != NS_OK) {
-        cudaEventSynchronize(L.ev);
-        cudaEventDestroy(L.ev);
+        cudaStreamSynchronize(es);
         for (SReq* q : rs) {
-            cudaFreeAsync(q->block, L.stream);
+            cudaEventDestroy(q->done_ev);
+            q->done_ev = nullptr;
+            put_block(S, q->block, q->block_bytes);
             q->block = nullptr;
             finish_req(S, q, r);
         }
-        cudaFreeAsync(L.block, L.stream);
+        cudaEventDestroy(L.up_ev);
+        cudaEventDestroy(L.h2d_ev);
+        cudaEventDestroy(L.exec_ev);
         S->pinned_free.push_back(L.staging);
+        put_block(S, L.block, L.block_bytes);
         return;
     }
     for (SReq* q : rs) q->state = 2;
+    L.reqs = order;
     S->launches.push_back(L);
+}
+
+// requests whose C has arrived are done; launches whose upload has finished give their staging
+// back; lock not held
+static void retire(Server* S)
+{
+    for (auto it = S->launches.begin(); it != S->launches.end();) {
+        SLaunch& L = *it;
+        if (L.up_ev && cudaEventQuery(L.up_ev) == cudaSuccess) {
+            cudaEventDestroy(L.up_ev);
+            L.up_ev = nullptr;
+            S->pinned_free.push_back(L.staging);
+            L.staging = Pinned{};
+        }
+        (void)cudaGetLastError();
+        size_t keep = 0;
+        for (size_t k = 0; k < L.reqs.size(); ++k) {
+            SReq* q = L.reqs[k];
+            if (cudaEventQuery(q->done_ev) != cudaSuccess) {
+                (void)cudaGetLastError();
+                L.reqs[keep++] = q;
+                continue;
+            }
+            // GPU completion times on the server clock
+            auto at = [&](cudaEvent_t e) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, S->ref_ev, e) != cudaSuccess) {
+                    (void)cudaGetLastError();
+                    return 0.0;
+                }
+                return S->t_ref + 1e-3 * ms;
+            };
+            q->st.t_h2d = at(L.h2d_ev);
+            q->st.t_exec = at(L.exec_ev);
+            q->st.t_d2h = at(q->done_ev);
+            cudaEventDestroy(q->done_ev);
+            q->done_ev = nullptr;
+            put_block(S, q->block, q->block_bytes);  // its C copy, hence the kernel, has completed
+            q->block = nullptr;
+            std::lock_guard<std::mutex> lk(S->mu);
+            finish_req(S, q, NS_OK);
+        }
+        L.reqs.resize(keep);
+        if (L.reqs.empty() && !L.up_ev) {
+            put_block(S, L.block, L.block_bytes);
+            cudaEventDestroy(L.h2d_ev);
+            cudaEventDestroy(L.exec_ev);
+            it = S->launches.erase(it);
+        } else {
+            ++it;
+        }
+    }
 }
 
 static void worker_loop(Server* S)
@@ -458,37 +637,18 @@ static void worker_loop(Server* S)
         }
         prepare(S, fresh, ready);
         if (!ready.empty()) {
-            cudaEvent_t copied;
-            cudaEventCreateWithFlags(&copied, cudaEventDisableTiming);
-            cudaEventRecord(copied, S->s_copy);
-            std::map<std::tuple<int, int, int, int, int>, std::vector<SReq*>> groups;
+            std::map<std::tuple<int, int, int, int, int, int>, std::vector<SReq*>> groups;
             for (SReq* q : ready) {
                 const Plan* P = q->sp->plan;
-                groups[{q->r.K, (int)q->r.b_dtype, P->st.n_dwin > 0 ? 1 : 0, P->tune.TM, P->tune.TK}].push_back(q);
+                groups[{q->cls, q->r.K, (int)q->r.b_dtype, P->st.n_dwin > 0 ? 1 : 0, P->tune.TM, P->tune.TK}]
+                    .push_back(q);
             }
-            for (auto& kv : groups)
-                launch_group(S, kv.second, std::get<0>(kv.first), std::get<1>(kv.first) == NS_BF16,
-                             std::get<2>(kv.first) != 0, std::get<3>(kv.first), std::get<4>(kv.first), copied);
-            cudaEventDestroy(copied);
+            for (auto& kv : groups)  // small class first
+                launch_group(S, kv.second, std::get<0>(kv.first), std::get<1>(kv.first),
+                             std::get<2>(kv.first) == NS_BF16, std::get<3>(kv.first) != 0, std::get<4>(kv.first),
+                             std::get<5>(kv.first));
         }
-        // ---- retire finished launches ----
-        for (auto it = S->launches.begin(); it != S->launches.end();) {
-            if (cudaEventQuery(it->ev) != cudaSuccess) {
-                (void)cudaGetLastError();
-                ++it;
-                continue;
-            }
-            std::lock_guard<std::mutex> lk(S->mu);
-            for (SReq* q : it->reqs) {
-                cudaFreeAsync(q->block, it->stream);
-                q->block = nullptr;
-                finish_req(S, q, NS_OK);
-            }
-            cudaEventDestroy(it->ev);
-            cudaFreeAsync(it->block, it->stream);
-            S->pinned_free.push_back(it->staging);
-            it = S->launches.erase(it);
-        }
+        retire(S);
     }
 }
 
@@ -523,9 +683,19 @@ ns_status_t ns_serve_create(const ns_serve_cfg_t* cfg, ns_server_t* out)
     S->cfg = *cfg;
     NS_CUDA_TRY(cudaGetDevice(&S->device));
     NS_CUDA_TRY(cudaStreamCreateWithFlags(&S->s_plan, cudaStreamNonBlocking));
-    NS_CUDA_TRY(cudaStreamCreateWithFlags(&S->s_copy, cudaStreamNonBlocking));
-    NS_CUDA_TRY(cudaStreamCreateWithFlags(&S->s_exec[0], cudaStreamNonBlocking));
-    NS_CUDA_TRY(cudaStreamCreateWithFlags(&S->s_exec[1], cudaStreamNonBlocking));
+    for (int c = 0; c < 2; ++c) {
+        NS_CUDA_TRY(cudaStreamCreateWithFlags(&S->s_copy[c], cudaStreamNonBlocking));
+        NS_CUDA_TRY(cudaStreamCreateWithFlags(&S->s_exec[c][0], cudaStreamNonBlocking));
+        NS_CUDA_TRY(cudaStreamCreateWithFlags(&S->s_exec[c][1], cudaStreamNonBlocking));
+    }
+    // the origin of GPU times: an event that completed just before t_ref
+    S->zeros_bytes = 1 << 20;
+    NS_CUDA_TRY(cudaHostAlloc(&S->zeros, S->zeros_bytes, cudaHostAllocDefault));
+    std::memset(S->zeros, 0, S->zeros_bytes);
+    NS_CUDA_TRY(cudaEventCreate(&S->ref_ev));
+    NS_CUDA_TRY(cudaEventRecord(S->ref_ev, S->s_exec[0][0]));
+    NS_CUDA_TRY(cudaEventSynchronize(S->ref_ev));
+    S->t_ref = serve_clock();
     S->worker = std::thread(worker_loop, S);
     S->planner = std::thread(planner_loop, S);
     *out = reinterpret_cast<ns_server_t>(S);
@@ -673,10 +843,15 @@ ns_status_t ns_serve_destroy(ns_server_t sv)
     for (auto& kv : S->plans) delete kv.second.plan;
     for (auto& kv : S->reqs) delete kv.second;
     for (auto& p : S->pinned_free) cudaFreeHost(p.p);
+    for (auto& kv : S->dev_free) cudaFree(kv.second);
+    cudaEventDestroy(S->ref_ev);
+    if (S->zeros) cudaFreeHost(S->zeros);
     cudaStreamDestroy(S->s_plan);
-    cudaStreamDestroy(S->s_copy);
-    cudaStreamDestroy(S->s_exec[0]);
-    cudaStreamDestroy(S->s_exec[1]);
+    for (int c = 0; c < 2; ++c) {
+        cudaStreamDestroy(S->s_copy[c]);
+        cudaStreamDestroy(S->s_exec[c][0]);
+        cudaStreamDestroy(S->s_exec[c][1]);
+    }
     delete S;
     return NS_OK;
 }

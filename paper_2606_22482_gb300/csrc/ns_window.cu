@@ -27,10 +27,19 @@ constexpr int kWinSmemKeys = 4096;  // windows up to this many elements sort in 
 constexpr int kMaxTM = 64;
 // Windows with more elements than kWinSmemKeys, of a matrix with at most kDenseCols columns, count
 // their columns in a per-CTA array instead of sorting: byte counters (TM <= 64 < 256) packed four
-// to a word, then 16-bit ascending positions (U <= n < 65536), 3 bytes per column in all.
+// to a word, then a presence bit per column and an ascending index per 32 columns (1.25 bytes a
+// column in all).
 constexpr int kDenseCols = 49152;
-constexpr int kEmitSmemWords = 4096;  // a window's dense-tile bitmaps assembled in shared memory
-constexpr int kEmitSmemTiles = 4096;  // and its tiles' dense ranks
+// counting path's shared memory: a byte counter per column (4 a word), a presence bit per column
+// and an index per 32 columns
+constexpr size_t count_table_bytes(int64_t n)
+{
+    return (size_t)4 * ((n + 3) / 4) + (size_t)8 * ((n + 31) / 32);
+}
+// emission assembles a window's dense-tile bitmaps (4 bytes a word), their per-tile prefix counts
+// (2 bytes a word) and its tiles' dense ranks (2 bytes a tile) in dynamic shared memory sized
+// from the plan's largest window, up to this limit (larger windows use global memory)
+constexpr int kEmitSmemMax = 192 * 1024;
 
 // ---------------------------------------------------------------------------------------------
 // W1: kept rows
@@ -100,17 +109,25 @@ __global__ void k_gather_window_elems(const int32_t* __restrict__ rowptr,
         int32_t i = __ldg(aic_rows + k);
         int64_t b = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
         int64_t out = row_kbase[k];
-        for (int64_t p0 = b; p0 < e; p0 += 32) {
-            int64_t p = p0 + lane;
-            int32_t c = p < e ? __ldg(colidx + p) : 0;
-            bool keep = p < e && (!colcount || __ldg(colcount + c) > tau_col);
-            unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                int64_t o = out + __popc(bal & ((1u << lane) - 1u));
-                ekey[o] = c;
-                eidx[o] = (int32_t)p;
+        for (int64_t p0 = b; p0 < e; p0 += 128) {  // four batches of 32 loads in flight
+            int32_t c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t p = p0 + 32 * u + lane;
+                c[u] = p < e ? __ldg(colidx + p) : 0;
             }
-            out += __popc(bal);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t p = p0 + 32 * u + lane;
+                const bool keep = p < e && (!colcount || __ldg(colcount + c[u]) > tau_col);
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int64_t o = out + __popc(bal & ((1u << lane) - 1u));
+                    ekey[o] = c[u];
+                    eidx[o] = (int32_t)p;
+                }
+                out += __popc(bal);
+            }
         }
     }
 }
@@ -256,7 +273,11 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
     extern __shared__ uint32_t dyn_cols[];
     const bool count_cols = a.count_cols && N > kWinSmemKeys;  // window-uniform
     const int nwords = (a.n + 3) >> 2;
-    uint16_t* const cpos = reinterpret_cast<uint16_t*>(dyn_cols + nwords);  // column -> ascending index
+    // after the counters: a presence bit per column and, per 32 columns, the ascending index of
+    // the first present one; a column's ascending index is then one lookup and a popcount
+    const int ngroups = (a.n + 31) >> 5;
+    uint32_t* const cbits = dyn_cols + nwords;
+    int32_t* const gpre = reinterpret_cast<int32_t*>(cbits + ngroups);
     if (count_cols) {
         // byte counters, four per word (a count is at most TM <= 64)
         for (int q = threadIdx.x; q < nwords; q += blockDim.x) dyn_cols[q] = 0u;
@@ -307,13 +328,23 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
                 const int f = present(wv);
                 const int inc = warp_incl_scan(f);
                 int64_t pre = base + inc - f;
+                // presence bits of the 32 columns of 8 consecutive words (q0 is a multiple of 32)
+                uint32_t bw = ((uint32_t)((wv & 0xffu) != 0) | ((uint32_t)((wv & 0xff00u) != 0) << 1) |
+                               ((uint32_t)((wv & 0xff0000u) != 0) << 2) | ((uint32_t)((wv & 0xff000000u) != 0) << 3))
+                              << (4 * (lane & 7));
+                bw |= __shfl_xor_sync(0xffffffffu, bw, 1);
+                bw |= __shfl_xor_sync(0xffffffffu, bw, 2);
+                bw |= __shfl_xor_sync(0xffffffffu, bw, 4);
+                if ((lane & 7) == 0 && q < whi) {
+                    cbits[q >> 3] = bw;
+                    gpre[q >> 3] = (int32_t)pre;
+                }
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
                     const uint32_t c = (wv >> (8 * b)) & 0xffu;
                     if (c) {
                         uasc[pre] = 4 * q + b;
                         ucnt[pre] = (int32_t)c;
-                        cpos[4 * q + b] = (uint16_t)pre;
                         ++pre;
                     }
                 }
@@ -412,7 +443,6 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
 
     // counting path: the column table now maps a column to its canonical position
     if (count_cols) {
-        for (int64_t u = threadIdx.x; u < U; u += blockDim.x) cpos[uasc[u]] = (uint16_t)upos[u];
         for (int q = threadIdx.x; q < kDenseCols / 16 / 32 + 1; q += blockDim.x) tdense[q] = 0u;
         __syncthreads();
     }
@@ -465,9 +495,11 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
                 for (int u = 0; u < 4; ++u) {
                     bool dense = false;
                     if (cv[u] >= 0) {
-                        const int32_t pos = cpos[cv[u]];
+                        const int32_t c = cv[u];
+                        const int32_t ai = gpre[c >> 5] + __popc(cbits[c >> 5] & ((1u << (c & 31)) - 1u));
+                        const int32_t pos = upos[ai];
                         epos[eb + 32 * u + lane] = pos;
-                        const int t = pos / TK;
+                        const int t = pos >> (TK == 32 ? 5 : 4);  // TK is 16 or 32
                         dense = (tdense[t >> 5] >> (t & 31)) & 1u;
                     }
                     cnt += __popc(__ballot_sync(0xffffffffu, dense));
@@ -480,7 +512,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
         const int32_t col = a.ekey[wbase + e];
         int64_t lo = 0, hi = U;  // ascending index of col: the counters' table, or a lower bound in uasc
         if (count_cols) {
-            lo = cpos[col];
+            lo = gpre[col >> 5] + __popc(cbits[col >> 5] & ((1u << (col & 31)) - 1u));
         } else {
             while (lo < hi) {
                 int64_t mid = (lo + hi) >> 1;
@@ -491,7 +523,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
         const int32_t pos = upos[lo];
         epos[e] = pos;
         // dense elements per row: one shared atomic per distinct row of the warp's 32 elements
-        const int slot = trank[pos / TK] >= 0 ? row_slot_of(rb0, nrows, e) : -1;
+        const int slot = trank[pos >> (TK == 32 ? 5 : 4)] >= 0 ? row_slot_of(rb0, nrows, e) : -1;
         const unsigned act = __activemask();
         const unsigned peers = __match_any_sync(act, slot);
         if (slot >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&dcnt[slot], __popc(peers));
@@ -620,7 +652,9 @@ struct EmitArgs {
     int32_t* dtile_voff;
     void* dtile_vals;
     uint8_t* pdense;  // per original element: 1 if in a dense tile
-    uint16_t* dtile_x;  // BF16 plans: each dense tile expanded to TM x TK values (zeros included)
+    int32_t cap_words;  // bitmap words and tiles a window may have for the shared-memory path
+    int32_t cap_tiles;
+    int32_t tk_log;     // log2(TK)
 };
 
 // Position of element (row r, compacted column c) inside an expanded TM x TK tile: 8 x 8 blocks
@@ -633,12 +667,15 @@ __host__ __device__ __forceinline__ int tile_x_offset(int r, int c, int TK)
     return (r >> 3) * (TK >> 3) * 64 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7);
 }
 
-__global__ void __launch_bounds__(kWinThreads) k_emit_tiles(EmitArgs a)
+__global__ void __launch_bounds__(kWinThreads, 4) k_emit_tiles(EmitArgs a)
 {
     __shared__ int64_t rb0[kMaxTM + 1];
-    __shared__ uint32_t sbits[kEmitSmemWords];
-    __shared__ int32_t wpre[kEmitSmemWords];
-    __shared__ int16_t srank[kEmitSmemTiles];
+    extern __shared__ __align__(16) unsigned char emit_smem[];
+    uint32_t* const sbits = reinterpret_cast<uint32_t*>(emit_smem);
+    int32_t* const stvoff = reinterpret_cast<int32_t*>(sbits + a.cap_words);
+    uint16_t* const wpre = reinterpret_cast<uint16_t*>(stvoff + a.cap_tiles);
+    int16_t* const srank = reinterpret_cast<int16_t*>(wpre + a.cap_words);
+    const int tkl = a.tk_log;
     const int w = blockIdx.x;
     if (a.win_ndt[w] == 0) return;
     const int TM = a.TM, TK = a.TK, BW = TM * TK / 32;
@@ -653,24 +690,28 @@ __global__ void __launch_bounds__(kWinThreads) k_emit_tiles(EmitArgs a)
     const int32_t ndt = a.win_ndt[w];
     // the window's dense-tile bitmaps (and tile ranks) in shared memory when they fit, else the
     // plan's bitmaps with global atomics and the ranks from global memory
-    const bool in_smem = (int64_t)ndt * BW <= kEmitSmemWords && ntile <= kEmitSmemTiles;
-    // columns and value offsets of the dense tiles
+    const bool in_smem = (int64_t)ndt * BW <= a.cap_words && ntile <= a.cap_tiles;
+    // ranks and value offsets of the tiles, value offsets of the dense tiles
     for (int64_t t = threadIdx.x; t < ntile; t += blockDim.x) {
-        int32_t k = a.trank[wbase + t];
-        if (in_smem) srank[t] = (int16_t)k;
-        if (k < 0) continue;
-        int64_t d = dbase + k;
-        for (int c = 0; c < TK; ++c) {
-            int64_t p = t * TK + c;
-            a.dtile_cols[d * TK + c] = p < U ? a.ucan[wbase + p] : -1;
+        const int32_t k = a.trank[wbase + t];
+        const int32_t tv = a.tvoff[wbase + t];
+        if (in_smem) {
+            srank[t] = (int16_t)k;
+            stvoff[t] = tv;
         }
-        a.dtile_voff[d] = (int32_t)(a.win_vbase[w] + a.tvoff[wbase + t]);
+        if (k >= 0) a.dtile_voff[dbase + k] = (int32_t)(a.win_vbase[w] + tv);
+    }
+    // columns of the dense tiles: one thread per (tile, column), reads of ucan coalesced
+    for (int64_t q = threadIdx.x; q < ntile * TK; q += blockDim.x) {
+        const int32_t k = a.trank[wbase + (q >> tkl)];
+        if (k < 0) continue;
+        a.dtile_cols[(int64_t)(dbase + k) * TK + (q & (TK - 1))] = q < U ? a.ucan[wbase + q] : -1;
     }
     if (in_smem)
         for (int q = threadIdx.x; q < ndt * BW; q += blockDim.x) sbits[q] = 0u;
     __syncthreads();
     auto rank_of = [&](int32_t pos) -> int32_t {
-        return in_smem ? (int32_t)srank[pos / TK] : a.trank[wbase + pos / TK];
+        return in_smem ? (int32_t)srank[pos >> tkl] : a.trank[wbase + (pos >> tkl)];
     };
     // bitmap bits: one warp per row of the window (the row of an element is its warp's row)
     for (int r = warp; r < nrows; r += nwarps) {
@@ -684,12 +725,30 @@ __global__ void __launch_bounds__(kWinThreads) k_emit_tiles(EmitArgs a)
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (pv[u] < 0) continue;
-                const int32_t k = rank_of(pv[u]);
-                if (k < 0) continue;
-                const int bit = r * TK + pv[u] % TK;
-                if (in_smem) atomicOr(&sbits[k * BW + bit / 32], 1u << (bit % 32));
-                else atomicOr(a.dtile_bits + (int64_t)(dbase + k) * BW + bit / 32, 1u << (bit % 32));
+                // consecutive elements of a row mostly set bits of one word: OR the bits of lanes
+                // with the same word together (segmented scan over runs of equal words), then one
+                // atomic per run instead of up to 32 on one address
+                int32_t key = -1;
+                uint32_t mbit = 0u;
+                if (pv[u] >= 0) {
+                    const int32_t k = rank_of(pv[u]);
+                    if (k >= 0) {
+                        const int bit = (r << tkl) + (pv[u] & (TK - 1));
+                        key = k * BW + (bit >> 5);
+                        mbit = 1u << (bit & 31);
+                    }
+                }
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t ko = __shfl_up_sync(0xffffffffu, key, o);
+                    const uint32_t mo = __shfl_up_sync(0xffffffffu, mbit, o);
+                    if (lane >= o && ko == key) mbit |= mo;
+                }
+                const int32_t kn = __shfl_down_sync(0xffffffffu, key, 1);
+                if (key >= 0 && (lane == 31 || kn != key)) {
+                    if (in_smem) atomicOr(&sbits[key], mbit);
+                    else atomicOr(a.dtile_bits + (int64_t)dbase * BW + key, mbit);
+                }
             }
         }
     }
@@ -698,9 +757,9 @@ __global__ void __launch_bounds__(kWinThreads) k_emit_tiles(EmitArgs a)
     if (in_smem) {
         for (int q = threadIdx.x; q < ndt * BW; q += blockDim.x) a.dtile_bits[(int64_t)dbase * BW + q] = sbits[q];
         for (int k = threadIdx.x; k < ndt; k += blockDim.x) {
-            int acc = 0;
+            int acc = 0;  // at most TM * TK = 2048 values a tile
             for (int q = 0; q < BW; ++q) {
-                wpre[k * BW + q] = acc;
+                wpre[k * BW + q] = (uint16_t)acc;
                 acc += __popc(sbits[k * BW + q]);
             }
         }
@@ -725,30 +784,98 @@ __global__ void __launch_bounds__(kWinThreads) k_emit_tiles(EmitArgs a)
             if (pos < 0) continue;
             const int32_t k = rank_of(pos);
             if (k < 0) continue;
-            const int32_t t = pos / TK;
-            const int bit = r * TK + pos % TK;
+            const int32_t t = pos >> tkl;
+            const int bit = (r << tkl) + (pos & (TK - 1));
             int idx = 0;
+            int32_t tv;
             if (in_smem) {
-                idx = wpre[k * BW + bit / 32] + __popc(sbits[k * BW + bit / 32] & ((1u << (bit % 32)) - 1u));
+                idx = wpre[k * BW + (bit >> 5)] + __popc(sbits[k * BW + (bit >> 5)] & ((1u << (bit & 31)) - 1u));
+                tv = stvoff[t];
             } else {
                 const uint32_t* bw = a.dtile_bits + (int64_t)(dbase + k) * BW;
-                for (int q = 0; q < bit / 32; ++q) idx += __popc(__ldcg(bw + q));
-                idx += __popc(__ldcg(bw + bit / 32) & ((1u << (bit % 32)) - 1u));
+                for (int q = 0; q < (bit >> 5); ++q) idx += __popc(__ldcg(bw + q));
+                idx += __popc(__ldcg(bw + (bit >> 5)) & ((1u << (bit & 31)) - 1u));
+                tv = a.tvoff[wbase + t];
             }
-            const int64_t vi = vbase + a.tvoff[wbase + t] + idx;
+            const int64_t vi = vbase + tv + idx;
             const float v = __ldg(a.vals + p);
             if (a.bf16) {
                 __nv_bfloat16 h = __float2bfloat16_rn(v);
                 const uint16_t hb = *reinterpret_cast<uint16_t*>(&h);
                 reinterpret_cast<uint16_t*>(a.dtile_vals)[vi] = hb;
-                if (a.dtile_x)
-                    a.dtile_x[(int64_t)(dbase + k) * TM * TK + tile_x_offset(r, pos % TK, TK)] = hb;
             } else {
                 reinterpret_cast<float*>(a.dtile_vals)[vi] = v;
             }
             a.pdense[p] = 1;
           }
         }
+    }
+}
+
+// W9b: BF16 plans, every dense tile expanded to TM x TK values (zeros included) in the tensor
+// cores' operand layout (tile_x_offset), from its bitmap and packed values.  One warp per tile:
+// the lanes take the bitmap's words in order, 32 bits at a time, so a warp's stores cover whole
+// 8-column groups of the expanded tile.
+__global__ void k_expand_tiles(const uint32_t* __restrict__ bits, const int32_t* __restrict__ voff,
+                               const uint16_t* __restrict__ vals, int64_t n_dtiles, int32_t TM, int32_t TK,
+                               uint16_t* __restrict__ x)
+{
+    const int lane = threadIdx.x & 31;
+    const int BW = TM * TK / 32;  // 8 .. 64 words
+    const int WPL = (BW + 31) / 32;  // words a lane sums for the prefix (1 or 2)
+    const int tkl = TK == 32 ? 5 : 4;
+    for (int64_t d = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < n_dtiles;
+         d += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const uint32_t* tb = bits + d * BW;
+        // exclusive prefix of the words' popcounts: lane owns words [lane WPL, lane WPL + WPL)
+        uint32_t wv[2] = {0u, 0u};
+        int own = 0;
+        for (int j = 0; j < WPL; ++j) {
+            const int q = lane * WPL + j;
+            wv[j] = q < BW ? __ldg(tb + q) : 0u;
+            own += __popc(wv[j]);
+        }
+        int incl = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int excl = incl - own;
+        const int64_t v0 = __ldg(voff + d);
+        uint16_t* tx = x + d * (int64_t)TM * TK;
+#pragma unroll 8
+        for (int q = 0; q < BW; ++q) {  // word q: bits 32 q .. 32 q + 31 of the row-major tile
+            const int src = WPL == 2 ? q >> 1 : q, j = WPL == 2 ? q & 1 : 0;
+            const uint32_t word = __shfl_sync(0xffffffffu, j == 0 ? wv[0] : wv[1], src);
+            int base = __shfl_sync(0xffffffffu, excl, src);
+            if (j == 1) base += __popc(__shfl_sync(0xffffffffu, wv[0], src));
+            const int b = 32 * q + lane;
+            const int r = b >> tkl, c = b & (TK - 1);
+            uint16_t v = 0;
+            if ((word >> lane) & 1u) v = __ldg(vals + v0 + base + __popc(word & ((1u << lane) - 1u)));
+            tx[tile_x_offset(r, c, TK)] = v;
+        }
+    }
+}
+
+// the largest window's dense tiles and tiles (emission's shared-memory sizing)
+__global__ void k_window_max(const int32_t* __restrict__ win_ndt, const int32_t* __restrict__ win_U, int64_t n_win,
+                             int32_t TK, int64_t* out)
+{
+    int64_t mt = 0, mu = 0;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_win; w += (int64_t)gridDim.x * blockDim.x) {
+        mt = max(mt, (int64_t)win_ndt[w]);
+        mu = max(mu, ((int64_t)win_U[w] + TK - 1) / TK);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mt = max(mt, __shfl_xor_sync(0xffffffffu, mt, o));
+        mu = max(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)mt);
+        atomicMax(reinterpret_cast<unsigned long long*>(out + 1), (unsigned long long)mu);
     }
 }
 
@@ -763,16 +890,25 @@ __global__ void k_residual_scatter(const int32_t* __restrict__ rowptr, const int
          i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         int64_t b = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
         int64_t out = res_rowptr[i];
-        for (int64_t p0 = b; p0 < e; p0 += 32) {
-            int64_t p = p0 + lane;
-            bool keep = p < e && !pdense[p];
-            unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                int64_t o = out + __popc(bal & ((1u << lane) - 1u));
-                res_col[o] = __ldg(colidx + p);
-                res_val[o] = __ldg(vals + p);
+        for (int64_t p0 = b; p0 < e; p0 += 128) {  // four batches of 32 loads in flight
+            uint8_t dn[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t p = p0 + 32 * u + lane;
+                dn[u] = p < e ? pdense[p] : 1;
             }
-            out += __popc(bal);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t p = p0 + 32 * u + lane;
+                const bool keep = p < e && !dn[u];
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int64_t o = out + __popc(bal & ((1u << lane) - 1u));
+                    res_col[o] = __ldg(colidx + p);
+                    res_val[o] = __ldg(vals + p);
+                }
+                out += __popc(bal);
+            }
         }
     }
 }
@@ -783,6 +919,13 @@ __global__ void k_fill_win_rows(const int32_t* __restrict__ aic_rows, int64_t m_
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < total;
          s += (int64_t)gridDim.x * blockDim.x)
         win_rows[s] = s < m_aic ? aic_rows[s] : -1;
+}
+
+static int32_t ilog2(int32_t v)
+{
+    int32_t l = 0;
+    while ((2 << l) <= v) ++l;
+    return l;
 }
 
 static unsigned wgrid(int64_t n, int threads = 256)
@@ -1022,14 +1165,14 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
                    sb0, sb1, uasc, ucnt, upos, ucan, ccnt, trank, tvoff, epos,
                    win_U, win_ndt, win_ndv, win_res, res_len, (int32_t)n, count_cols ? 1 : 0};
         // the counting table (3 bytes a column) or the two sort buffers, whichever is larger
-        const size_t tbl = count_cols ? (size_t)3 * (((n + 3) / 4) * 4) : 0;
+        const size_t tbl = count_cols ? count_table_bytes(n) : 0;
         const size_t keys = (size_t)2 * kWinSmemKeys * sizeof(int32_t);
         const size_t dyn = tbl > keys ? tbl : keys;
         // static + dynamic shared memory above 48 KB needs the opt-in; one fixed limit (the largest
         // counting table) keeps concurrent planners from lowering it under each other's launches
-        static_assert(3 * kDenseCols >= 2 * kWinSmemKeys * 4, "sort buffers fit the opt-in limit");
+        static_assert(count_table_bytes(kDenseCols) >= 2 * kWinSmemKeys * 4, "sort buffers fit the opt-in limit");
         NS_CUDA_TRY(cudaFuncSetAttribute(k_window_compact, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         3 * kDenseCols));
+                                         (int)count_table_bytes(kDenseCols)));
         k_window_compact<<<(unsigned)n_win, kWinThreads, dyn, s>>>(wa);
         NS_LAUNCH_CHECK();
     }
@@ -1040,10 +1183,15 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
     NS_TRY(device_scan<int64_t>(I32Load{win_ndv}, PtrStore64{win_vbase}, n_win, partial, totals + 2, s));
     NS_TRY(device_scan<int64_t>(DenseWinLoad{win_ndt}, DenseWinStore{P->dwin}, n_win, partial, totals + 3, s));
     NS_TRY(device_scan<int64_t>(I32Load{res_len}, PtrStore32{P->res_rowptr_own}, m, part2, totals + 4, s));
+    if (n_win > 0) {
+        k_window_max<<<wgrid(n_win), 256, 0, s>>>(win_ndt, win_U, n_win, TK, totals + 6);
+        NS_LAUNCH_CHECK();
+    }
     int64_t ht[8];
     NS_CUDA_TRY(cudaMemcpyAsync(ht, totals, sizeof ht, cudaMemcpyDeviceToHost, s));
     NS_CUDA_TRY(cudaStreamSynchronize(s));
     const int64_t n_dtiles = ht[1], n_dvals = ht[2], n_dwin = ht[3], n_res = ht[4];
+    const int64_t max_ndt = ht[6], max_ntile = ht[7];
     P->st.n_dtiles = n_dtiles;
     P->st.n_dvals = n_dvals;
     P->st.n_dwin = n_dwin;
@@ -1083,18 +1231,35 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
     NS_CUDA_TRY(cudaMemsetAsync(P->dtile_bits, 0, sizeof(uint32_t) * (n_dtiles * BW > 0 ? n_dtiles * BW : 1), s));
     NS_CUDA_TRY(cudaMemsetAsync(P->dtile_vals, 0, (size_t)(n_dvals > 0 ? n_dvals : 1) * (bf16 ? 2 : 4), s));
     NS_CUDA_TRY(cudaMemsetAsync(pdense, 0, (size_t)(nnz > 0 ? nnz : 1), s));
-    if (bf16 && n_dtiles > 0)
-        NS_CUDA_TRY(cudaMemsetAsync(P->dtile_x, 0, sizeof(uint16_t) * n_dtiles * TM * TK, s));
     {
         int32_t v32 = (int32_t)n_dvals;
         NS_CUDA_TRY(cudaMemcpyAsync(P->dtile_voff + n_dtiles, &v32, sizeof v32, cudaMemcpyHostToDevice, s));
     }
     if (n_dtiles > 0) {
+        // shared memory for the largest window, or for as much as fits the limit
+        int64_t cap_tiles = max_ntile, cap_words = max_ndt * BW;
+        if (cap_tiles * 6 + cap_words * 6 > kEmitSmemMax) {
+            cap_tiles = cap_tiles * 6 <= kEmitSmemMax / 4 ? cap_tiles : kEmitSmemMax / 24;
+            cap_words = (kEmitSmemMax - cap_tiles * 6) / 6;
+        }
+        cap_words &= ~int64_t(3);  // keeps the tiles' offsets 16-byte aligned
+        const size_t dyn = (size_t)(cap_words * 6 + cap_tiles * 6 + 16);
+        // one fixed opt-in limit, so concurrent planners never lower it under each other
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_emit_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kEmitSmemMax + 16));
         EmitArgs ea{row_kbase, eidx, epos, ucan, trank, tvoff, win_U, win_ndt, P->win_dptr, win_vbase,
                     P->vals, m_aic, TM, TK, bf16 ? 1 : 0, P->dtile_cols, P->dtile_bits, P->dtile_voff,
-                    P->dtile_vals, pdense, bf16 ? P->dtile_x : nullptr};
-        k_emit_tiles<<<(unsigned)n_win, kWinThreads, 0, s>>>(ea);
+                    P->dtile_vals, pdense, (int32_t)cap_words, (int32_t)cap_tiles, ilog2(TK)};
+        k_emit_tiles<<<(unsigned)n_win, kWinThreads, dyn, s>>>(ea);
         NS_LAUNCH_CHECK();
+        if (bf16) {
+            const int64_t warps = n_dtiles;
+            const int64_t blocks = (warps * 32 + 255) / 256;
+            k_expand_tiles<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(
+                P->dtile_bits, P->dtile_voff, reinterpret_cast<const uint16_t*>(P->dtile_vals), n_dtiles, TM, TK,
+                P->dtile_x);
+            NS_LAUNCH_CHECK();
+        }
     }
     if (m > 0) {
         k_residual_scatter<<<wgrid(m * 32), 256, 0, s>>>(P->rowptr, P->colidx, P->vals, pdense,

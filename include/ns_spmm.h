@@ -203,7 +203,7 @@ typedef struct {
 } ns_tune_report_t;
 
 /* Dry runs on A give p_res (residual-only plan) and p_tc (every compacted tile dense), hence
- * alpha0 and tau0 = ceil(alpha0 * TM * TK); then (TM, tau) candidates around tau0, the two
+ * alpha0 and tau0 = ceil(alpha0 * TM * TK); then (TM, TK, tau) candidates around tau0, the two
  * single-engine extremes and column slices TN are planned and timed, and the best by
  * execute_ms + plan_ms / plan_runs is returned in *out.  A must be on the device.  Synchronous;
  * report may be NULL (then plan_runs = 200). */

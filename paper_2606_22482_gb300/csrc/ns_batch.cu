@@ -384,6 +384,27 @@ static ns_status_t time_tune(const ns_csr_t* A, int32_t K, ns_dtype_t dt, const 
     return r;
 }
 
+// A fresh plan for every execute: the whole cycle (plan, execute, release), best of two, which is
+// what a caller that re-plans every step pays (launch gaps and the release included).
+static ns_status_t time_cycle(const ns_csr_t* A, int32_t K, ns_dtype_t dt, const ns_tune_t& t,
+                              const void* Bd, float* Cd, cudaStream_t st, double* cycle_ms)
+{
+    double best = 1e30;
+    for (int rep = 0; rep < 2; ++rep) {
+        const double t0 = now_s();
+        Plan* P = nullptr;
+        NS_TRY(plan_create(A, K, dt, &t, st, &P));
+        ns_status_t r = ns_spmm_execute(reinterpret_cast<ns_plan_t>(P), Bd, K, Cd, K, st);
+        delete P;
+        if (r != NS_OK) return r;
+        NS_CUDA_TRY(cudaStreamSynchronize(st));
+        const double ms = (now_s() - t0) * 1e3;
+        if (ms < best) best = ms;
+    }
+    *cycle_ms = best;
+    return NS_OK;
+}
+
 int32_t ns_rebalance_next(int32_t lo, int32_t hi, int32_t tau, double dt_tc, double dt_res, double eps,
                           int32_t* lo_out, int32_t* hi_out, int32_t* tau_out)
 {
@@ -514,6 +535,10 @@ ns_status_t ns_autotune(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, ns_str
     double best_cost = 1e300, best_exec = 0;
     auto consider = [&](const ns_tune_t& t, double ex, double pl) {
         double c = ex + pl / amort;
+        if (amort <= 1.0) {  // re-planned every execute: time the whole cycle as the caller runs it
+            double cyc = 0;
+            if (time_cycle(A, K, b_dtype, t, Bd, Cd, st, &cyc) == NS_OK) c = cyc;
+        }
         ++trials;
         if (c < best_cost) {
             best_cost = c;
@@ -555,21 +580,25 @@ ns_status_t ns_autotune(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, ns_str
     }
     const double alpha0 = p_tc > 0 ? p_res / p_tc : 1.0;
 
-    // sweeps: window height x tau around tau0 (Section 8 threshold and tile-size studies)
+    // sweeps: tile shape (window height x compacted width) x tau around tau0 (Section 8
+    // threshold and tile-size studies)
     const int TMs[3] = {16, 32, 64};
+    const int TKs[2] = {16, 32};
     const double mult[5] = {0.5, 0.75, 1.0, 1.5, 2.0};
+    for (int TK : TKs)
     for (int TM : TMs) {
         if ((int64_t)TM * K > 16384) continue;
-        int32_t tau0 = ns_cost_tau(alpha0, TM, base.TK);
+        int32_t tau0 = ns_cost_tau(alpha0, TM, TK);
         int32_t last = -1;
         for (double mu : mult) {
             int32_t tau = (int32_t)std::ceil(mu * tau0);
             if (tau < 2) tau = 2;
-            if (tau > TM * base.TK) tau = TM * base.TK;
+            if (tau > TM * TK) tau = TM * TK;
             if (tau == last) continue;
             last = tau;
             ns_tune_t t = base;
             t.TM = TM;
+            t.TK = TK;
             t.tau_tile = tau;
             double ex = 0, pl = 0;
             r = time_tune(A, K, b_dtype, t, Bd, Cd, st, &ex, &pl, nullptr);

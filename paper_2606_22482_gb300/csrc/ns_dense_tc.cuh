@@ -35,10 +35,13 @@
 namespace ns {
 
 constexpr int kTcMaxStages = 16;
-constexpr int kTcRingBytes = 72 * 1024;  // ring budget: two CTAs per SM with the result tile
+// ring budget: three CTAs per SM with the result tile (measured on the attention shape, TM 64,
+// TK 32: 0.153 ms per execute at three CTAs with a 3-stage ring, 0.191 ms at two CTAs with a 6- or
+// 4-stage ring; resident windows hide the gathers' latency better than deeper rings)
+constexpr int kTcRingBytes = 36 * 1024;
 constexpr int kTcTmemCols = 128;         // two feature blocks x TM <= 64 columns of FP32 accumulators
 constexpr int kTcProducers = kExecThreads - 32;  // warps 1..3 copy; warp 0 issues the MMAs
-constexpr int kTcLag = 4;  // tiles a producer thread keeps in flight before it signals the oldest
+constexpr int kTcLag = 2;  // tiles a producer thread keeps in flight before it signals the oldest
 
 struct TcGeom {
     int FB;           // feature blocks of 128 (ceil(K / 128))

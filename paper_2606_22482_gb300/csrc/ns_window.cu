@@ -635,7 +635,7 @@ struct RlStore {
 // ---------------------------------------------------------------------------------------------
 struct EmitArgs {
     const int64_t* row_kbase;
-    const int32_t* eidx;
+    const int32_t* eidx;  // CSR position of each window element; NULL: element e is position e
     const int32_t* epos;
     const int32_t* ucan;
     const int32_t* trank;
@@ -655,6 +655,8 @@ struct EmitArgs {
     int32_t cap_words;  // bitmap words and tiles a window may have for the shared-memory path
     int32_t cap_tiles;
     int32_t tk_log;     // log2(TK)
+    uint16_t* dtile_x;  // BF16 plans: the values go straight into the expanded tiles (zeroed
+                        // beforehand) and k_pack_tiles packs them afterwards; NULL: packed here
 };
 
 // Position of element (row r, compacted column c) inside an expanded TM x TK tile: 8 x 8 blocks
@@ -717,11 +719,12 @@ __global__ void __launch_bounds__(kWinThreads, 4) k_emit_tiles(EmitArgs a)
     for (int r = warp; r < nrows; r += nwarps) {
         const int64_t rend = rb0[r + 1];
         for (int64_t eb = rb0[r]; eb < rend; eb += 128) {  // four positions per lane in flight
-            int32_t pv[4];
+            int32_t pv[4], iv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int64_t e = eb + 32 * u + lane;
                 pv[u] = e < rend ? a.epos[wbase + e] : -1;
+                if (a.dtile_x) iv[u] = e < rend ? (a.eidx ? a.eidx[wbase + e] : (int32_t)(wbase + e)) : -1;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -736,6 +739,13 @@ __global__ void __launch_bounds__(kWinThreads, 4) k_emit_tiles(EmitArgs a)
                         const int bit = (r << tkl) + (pv[u] & (TK - 1));
                         key = k * BW + (bit >> 5);
                         mbit = 1u << (bit & 31);
+                        if (a.dtile_x) {  // BF16: the value into its expanded tile
+                            const float v = __ldg(a.vals + iv[u]);
+                            __nv_bfloat16 h = __float2bfloat16_rn(v);
+                            a.dtile_x[(int64_t)(dbase + k) * TM * TK + tile_x_offset(r, pv[u] & (TK - 1), TK)] =
+                                *reinterpret_cast<uint16_t*>(&h);
+                            a.pdense[iv[u]] = 1;
+                        }
                     }
                 }
 #pragma unroll
@@ -753,6 +763,11 @@ __global__ void __launch_bounds__(kWinThreads, 4) k_emit_tiles(EmitArgs a)
         }
     }
     __syncthreads();
+    if (a.dtile_x) {  // BF16: values already placed; k_pack_tiles packs them from the tiles
+        if (in_smem)
+            for (int q = threadIdx.x; q < ndt * BW; q += blockDim.x) a.dtile_bits[(int64_t)dbase * BW + q] = sbits[q];
+        return;
+    }
     // per dense tile, the value index of each bitmap word's first bit
     if (in_smem) {
         for (int q = threadIdx.x; q < ndt * BW; q += blockDim.x) a.dtile_bits[(int64_t)dbase * BW + q] = sbits[q];
@@ -775,7 +790,7 @@ __global__ void __launch_bounds__(kWinThreads, 4) k_emit_tiles(EmitArgs a)
           for (int u = 0; u < 4; ++u) {
               const int64_t e = eb + 32 * u + lane;
               pv[u] = e < rend ? a.epos[wbase + e] : -1;
-              iv[u] = e < rend ? a.eidx[wbase + e] : -1;
+              iv[u] = e < rend ? (a.eidx ? a.eidx[wbase + e] : (int32_t)(wbase + e)) : -1;
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -812,22 +827,21 @@ __global__ void __launch_bounds__(kWinThreads, 4) k_emit_tiles(EmitArgs a)
     }
 }
 
-// W9b: BF16 plans, every dense tile expanded to TM x TK values (zeros included) in the tensor
-// cores' operand layout (tile_x_offset), from its bitmap and packed values.  One warp per tile:
-// the lanes take the bitmap's words in order, 32 bits at a time, so a warp's stores cover whole
-// 8-column groups of the expanded tile.
-__global__ void k_expand_tiles(const uint32_t* __restrict__ bits, const int32_t* __restrict__ voff,
-                               const uint16_t* __restrict__ vals, int64_t n_dtiles, int32_t TM, int32_t TK,
-                               uint16_t* __restrict__ x)
+// W9b: BF16 plans, packed values from the expanded tiles (emission wrote each value straight into
+// its tile at tile_x_offset).  One warp per tile: the lanes take the bitmap's words in order, 32
+// bits at a time; a set bit's value goes to its rank in bitmap order (the words' popcounts scanned
+// across the lanes, plus the bits before it in its word).
+__global__ void k_pack_tiles(const uint32_t* __restrict__ bits, const int32_t* __restrict__ voff,
+                             const uint16_t* __restrict__ x, int64_t n_dtiles, int32_t TM, int32_t TK,
+                             uint16_t* __restrict__ vals)
 {
     const int lane = threadIdx.x & 31;
-    const int BW = TM * TK / 32;  // 8 .. 64 words
-    const int WPL = (BW + 31) / 32;  // words a lane sums for the prefix (1 or 2)
+    const int BW = TM * TK / 32;
+    const int WPL = (BW + 31) / 32;
     const int tkl = TK == 32 ? 5 : 4;
     for (int64_t d = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < n_dtiles;
          d += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const uint32_t* tb = bits + d * BW;
-        // exclusive prefix of the words' popcounts: lane owns words [lane WPL, lane WPL + WPL)
         uint32_t wv[2] = {0u, 0u};
         int own = 0;
         for (int j = 0; j < WPL; ++j) {
@@ -843,18 +857,17 @@ __global__ void k_expand_tiles(const uint32_t* __restrict__ bits, const int32_t*
         }
         const int excl = incl - own;
         const int64_t v0 = __ldg(voff + d);
-        uint16_t* tx = x + d * (int64_t)TM * TK;
+        const uint16_t* tx = x + d * (int64_t)TM * TK;
 #pragma unroll 8
-        for (int q = 0; q < BW; ++q) {  // word q: bits 32 q .. 32 q + 31 of the row-major tile
+        for (int q = 0; q < BW; ++q) {
             const int src = WPL == 2 ? q >> 1 : q, j = WPL == 2 ? q & 1 : 0;
             const uint32_t word = __shfl_sync(0xffffffffu, j == 0 ? wv[0] : wv[1], src);
             int base = __shfl_sync(0xffffffffu, excl, src);
             if (j == 1) base += __popc(__shfl_sync(0xffffffffu, wv[0], src));
-            const int b = 32 * q + lane;
-            const int r = b >> tkl, c = b & (TK - 1);
-            uint16_t v = 0;
-            if ((word >> lane) & 1u) v = __ldg(vals + v0 + base + __popc(word & ((1u << lane) - 1u)));
-            tx[tile_x_offset(r, c, TK)] = v;
+            if ((word >> lane) & 1u) {
+                const int b = 32 * q + lane;
+                vals[v0 + base + __popc(word & ((1u << lane) - 1u))] = tx[tile_x_offset(b >> tkl, b & (TK - 1), TK)];
+            }
         }
     }
 }
@@ -1125,14 +1138,22 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
     P->blocks.push_back(pa.take());
     P->res_rowptr = P->res_rowptr_own;
 
+    // Every row kept, in order, with all its columns: the window elements are A's own column
+    // array in CSR order, so the element gather is skipped (element e is CSR position e).
+    const bool ident = m_aic == m && t.reorder <= 0 && t.tau_col <= 0 && nnz_win == nnz;
     Arena tw;  // window temporaries (freed when planning ends)
-    int32_t *ekey, *eidx, *sb0, *sb1, *uasc, *ucnt, *upos, *ucan, *ccnt, *trank, *tvoff, *epos;
+    int32_t *ekey = nullptr, *eidx = nullptr;
+    int32_t *sb0, *sb1, *uasc, *ucnt, *upos, *ucan, *ccnt, *trank, *tvoff, *epos;
     int32_t *win_U, *win_ndt, *win_ndv, *res_len;
     int64_t *win_res, *win_vbase, *part2;
     int8_t* row_state;
     int64_t* dcost;
     uint8_t* pdense;
-    for (int32_t** q : {&ekey, &eidx, &sb0, &sb1, &uasc, &ucnt, &upos, &ucan, &ccnt, &trank, &tvoff, &epos})
+    if (!ident) {
+        tw.reserve(&ekey, nnz_win);
+        tw.reserve(&eidx, nnz_win);
+    }
+    for (int32_t** q : {&sb0, &sb1, &uasc, &ucnt, &upos, &ucan, &ccnt, &trank, &tvoff, &epos})
         tw.reserve(q, nnz_win);
     tw.reserve(&win_U, n_win);
     tw.reserve(&win_ndt, n_win);
@@ -1153,15 +1174,17 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
         NS_CUDA_TRY(cudaMemcpyAsync(P->aic_rows, aic_rows, sizeof(int32_t) * m_aic, cudaMemcpyDeviceToDevice, s));
         k_fill_win_rows<<<wgrid(n_win * TM), 256, 0, s>>>(aic_rows, m_aic, n_win * TM, P->win_rows);
         NS_LAUNCH_CHECK();
-        k_gather_window_elems<<<wgrid(m_aic * 32), 256, 0, s>>>(P->rowptr, P->colidx, aic_rows, m_aic,
-                                                               row_kbase, colcount, t.tau_col, ekey, eidx);
-        NS_LAUNCH_CHECK();
+        if (!ident) {
+            k_gather_window_elems<<<wgrid(m_aic * 32), 256, 0, s>>>(P->rowptr, P->colidx, aic_rows, m_aic,
+                                                                   row_kbase, colcount, t.tau_col, ekey, eidx);
+            NS_LAUNCH_CHECK();
+        }
     }
     k_res_len_free_rows<<<wgrid(m), 256, 0, s>>>(P->rowptr, m, t.tau_row, res_len);
     NS_LAUNCH_CHECK();
     if (n_win > 0) {
         const bool count_cols = n <= kDenseCols;
-        WinArgs wa{P->rowptr, aic_rows, row_kbase, ekey, m_aic, TM, TK, t.tau_tile, t.col_order,
+        WinArgs wa{P->rowptr, aic_rows, row_kbase, ident ? P->colidx : ekey, m_aic, TM, TK, t.tau_tile, t.col_order,
                    sb0, sb1, uasc, ucnt, upos, ucan, ccnt, trank, tvoff, epos,
                    win_U, win_ndt, win_ndv, win_res, res_len, (int32_t)n, count_cols ? 1 : 0};
         // the counting table (3 bytes a column) or the two sort buffers, whichever is larger
@@ -1249,15 +1272,17 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
                                          kEmitSmemMax + 16));
         EmitArgs ea{row_kbase, eidx, epos, ucan, trank, tvoff, win_U, win_ndt, P->win_dptr, win_vbase,
                     P->vals, m_aic, TM, TK, bf16 ? 1 : 0, P->dtile_cols, P->dtile_bits, P->dtile_voff,
-                    P->dtile_vals, pdense, (int32_t)cap_words, (int32_t)cap_tiles, ilog2(TK)};
+                    P->dtile_vals, pdense, (int32_t)cap_words, (int32_t)cap_tiles, ilog2(TK),
+                    bf16 ? P->dtile_x : nullptr};
+        if (bf16) NS_CUDA_TRY(cudaMemsetAsync(P->dtile_x, 0, sizeof(uint16_t) * n_dtiles * TM * TK, s));
         k_emit_tiles<<<(unsigned)n_win, kWinThreads, dyn, s>>>(ea);
         NS_LAUNCH_CHECK();
         if (bf16) {
             const int64_t warps = n_dtiles;
             const int64_t blocks = (warps * 32 + 255) / 256;
-            k_expand_tiles<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(
-                P->dtile_bits, P->dtile_voff, reinterpret_cast<const uint16_t*>(P->dtile_vals), n_dtiles, TM, TK,
-                P->dtile_x);
+            k_pack_tiles<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(
+                P->dtile_bits, P->dtile_voff, P->dtile_x, n_dtiles, TM, TK,
+                reinterpret_cast<uint16_t*>(P->dtile_vals));
             NS_LAUNCH_CHECK();
         }
     }

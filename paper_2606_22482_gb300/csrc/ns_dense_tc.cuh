@@ -38,8 +38,9 @@ constexpr int kTcMaxStages = 16;
 // ring budget: three CTAs per SM with the result tile (measured on the attention shape, TM 64,
 // TK 32: 0.153 ms per execute at three CTAs with a 3-stage ring, 0.191 ms at two CTAs with a 6- or
 // 4-stage ring; resident windows hide the gathers' latency better than deeper rings)
-constexpr int kTcRingBytes = 36 * 1024;
+constexpr int kTcRingBytes = 36 * 1024;  // (the result tile shares it: four CTAs per SM)
 constexpr int kTcTmemCols = 128;         // two feature blocks x TM <= 64 columns of FP32 accumulators
+constexpr int kTcCtasPerSm = 512 / kTcTmemCols;  // CTAs whose tensor memory fits an SM's 512 columns
 constexpr int kTcProducers = kExecThreads - 32;  // warps 1..3 copy; warp 0 issues the MMAs
 constexpr int kTcLag = 2;  // tiles a producer thread keeps in flight before it signals the oldest
 
@@ -49,7 +50,8 @@ struct TcGeom {
     int b_bytes;      // gathered B rows of one tile, all feature blocks
     int stage_bytes;  // one ring stage (A, then B), 128-byte aligned
     int S;            // ring stages (as many as the ring budget holds, kTcLag + 1 .. kTcMaxStages)
-    int off_c;        // TM x cs_stride FP32 result tile
+    int off_c;        // TM x cs_stride FP32 result tile (shares the ring: written only once the
+                      // window's MMAs have completed and its producers are done)
     int cs_stride;
     int total;
 };
@@ -65,8 +67,9 @@ __host__ __device__ inline TcGeom tc_geom(int K, int TM, int TK)
     if (g.S > kTcMaxStages) g.S = kTcMaxStages;
     if (g.S < kTcLag + 1) g.S = kTcLag + 1;  // the ring holds every tile a producer has in flight
     g.cs_stride = K + 4;
-    g.off_c = g.S * g.stage_bytes;
-    g.total = g.off_c + ((TM * g.cs_stride * 4 + 127) & ~127);
+    g.off_c = 0;
+    const int ring = g.S * g.stage_bytes, cs = (TM * g.cs_stride * 4 + 127) & ~127;
+    g.total = ring > cs ? ring : cs;
     return g;
 }
 
@@ -316,6 +319,9 @@ __device__ bool tc_window_product(const ExecDesc& D, int32_t w, unsigned char* s
     }
     S.gi = g0 + (uint32_t)T;
     tc_fence_after();
+    // the result tile overwrites the ring the MMAs read through the async proxy: order those
+    // reads (complete, as the barrier wait above showed) before this thread's generic writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     // accumulator -> shared result tile: warp w reads TMEM lanes 32w..32w+31 (features), 16
     // columns (rows) at a time
     for (int fb = 0; fb < G.FB; ++fb) {

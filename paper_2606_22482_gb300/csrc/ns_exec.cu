@@ -1205,6 +1205,8 @@ ns_status_t exec_prepare(int64_t n_items, int K, int TM, int TK, bool bf16, bool
         const int fit = by_smem < by_regs ? by_smem : by_regs;
         if (fit > per_sm) per_sm = fit;
     }
+    // the tensor-core item allocates tensor memory per CTA: no more CTAs per SM than it holds
+    if (dense && bf16 && tc_supported(K) && per_sm > kTcCtasPerSm) per_sm = kTcCtasPerSm;
     if (per_sm < 1) per_sm = 1;
     int64_t g = (int64_t)per_sm * num_sms(dev);
     if (g > n_items) g = n_items;

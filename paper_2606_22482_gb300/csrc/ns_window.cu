@@ -32,9 +32,11 @@ constexpr int kMaxTM = 64;
 constexpr int kDenseCols = 49152;
 // counting path's shared memory: a byte counter per column (4 a word), a presence bit per column
 // and an index per 32 columns
+// and, for windows of up to kCanonSmem distinct columns, each column's canonical position (16 bits)
+constexpr int kCanonSmem = 16384;
 constexpr size_t count_table_bytes(int64_t n)
 {
-    return (size_t)4 * ((n + 3) / 4) + (size_t)8 * ((n + 31) / 32);
+    return (size_t)4 * ((n + 3) / 4) + (size_t)8 * ((n + 31) / 32) + (size_t)2 * kCanonSmem;
 }
 // emission assembles a window's dense-tile bitmaps (4 bytes a word), their per-tile prefix counts
 // (2 bytes a word) and its tiles' dense ranks (2 bytes a tile) in dynamic shared memory sized
@@ -224,7 +226,7 @@ struct WinArgs {
     int64_t* win_res;   // residual nonzeros of the window's rows
     int32_t* res_len;   // per row (m)
     int32_t n;          // columns of A
-    int32_t count_cols; // 1: launched with 3 * round4(n) bytes of dynamic shared memory (n <= kDenseCols)
+    int32_t count_cols; // 1: launched with count_table_bytes(n) bytes of dynamic shared memory (n <= kDenseCols)
 };
 
 // row slot of window element e: the largest r < nrows with rb[r] <= e (empty rows share their
@@ -278,6 +280,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
     const int ngroups = (a.n + 31) >> 5;
     uint32_t* const cbits = dyn_cols + nwords;
     int32_t* const gpre = reinterpret_cast<int32_t*>(cbits + ngroups);
+    uint16_t* const scan = reinterpret_cast<uint16_t*>(gpre + ngroups);  // canonical position by ascending index
     if (count_cols) {
         // byte counters, four per word (a count is at most TM <= 64)
         for (int q = threadIdx.x; q < nwords; q += blockDim.x) dyn_cols[q] = 0u;
@@ -393,6 +396,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
     if (a.col_order == 1) {
         for (int64_t u = threadIdx.x; u < U; u += blockDim.x) {
             upos[u] = (int32_t)u;
+            if (count_cols && U <= kCanonSmem) scan[u] = (uint16_t)u;
             ucan[u] = uasc[u];
             ccnt[u] = ucnt[u];
         }
@@ -427,6 +431,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
                 for (int q = 0; q < warp; ++q) before += wc[q][c];
                 int32_t dest = binoff[c] + before + rk;
                 upos[u] = dest;
+                if (count_cols && U <= kCanonSmem) scan[u] = (uint16_t)dest;
                 ucan[dest] = uasc[u];
                 ccnt[dest] = c;
             }
@@ -497,7 +502,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_compact(WinArgs a)
                     if (cv[u] >= 0) {
                         const int32_t c = cv[u];
                         const int32_t ai = gpre[c >> 5] + __popc(cbits[c >> 5] & ((1u << (c & 31)) - 1u));
-                        const int32_t pos = upos[ai];
+                        const int32_t pos = U <= kCanonSmem ? (int32_t)scan[ai] : upos[ai];
                         epos[eb + 32 * u + lane] = pos;
                         const int t = pos >> (TK == 32 ? 5 : 4);  // TK is 16 or 32
                         dense = (tdense[t >> 5] >> (t & 31)) & 1u;

@@ -960,8 +960,16 @@ static unsigned wgrid(int64_t n, int threads = 256)
 // unassigned row anchors a window and takes the TM - 1 unassigned rows with the largest Jaccard
 // similarity of kept-column sets (earlier rows first on ties), best first.  Similarities are
 // compared exactly as fractions (cross products in 64 bits).
+//
+// The intersections |cols(anchor) & cols(b)| come from an index of the cluster's kept entries
+// by column: a hash table of chains in shared memory (heads) with the chain links and each
+// entry's row in global scratch indexed by the entry's CSR position (clusters own disjoint
+// rows, hence disjoint positions).  For an anchor, each of its kept columns walks its chain and
+// counts one for every unassigned row holding that column, so the work per anchor is the number
+// of entries sharing a column with it, not the cluster's size times the rows' lengths.
 // ---------------------------------------------------------------------------------------------
 constexpr int kReorderThreads = 256;
+constexpr int kReorderHash = 4096;  // chain heads per cluster (power of two)
 
 struct SimKey {
     int64_t num, den;  // Jaccard = num / den (0 / 1 for two empty sets)
@@ -976,14 +984,22 @@ __device__ __forceinline__ bool sim_better(const SimKey& x, const SimKey& y)
     return l > r || (l == r && x.pos < y.pos);
 }
 
+__device__ __forceinline__ uint32_t col_hash(int32_t c)
+{
+    return ((uint32_t)c * 2654435761u) >> (32 - 12);  // 12 bits: kReorderHash buckets
+}
+
 __global__ void __launch_bounds__(kReorderThreads) k_local_reorder(
     const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
     const int32_t* __restrict__ colcount, int32_t tau_col, const int32_t* __restrict__ aic_in,
-    int64_t m_aic, int TM, int CR, int32_t* __restrict__ aic_out)
+    int64_t m_aic, int TM, int CR, int32_t* __restrict__ aic_out, int32_t* __restrict__ link,
+    int16_t* __restrict__ erow)
 {
+    static_assert(kReorderHash == 1 << 12, "col_hash yields 12 bits");
     __shared__ uint8_t used[kReorderMaxRows];
     __shared__ int32_t klen[kReorderMaxRows];
     __shared__ int32_t inter[kReorderMaxRows];
+    __shared__ int32_t head[kReorderHash];
     __shared__ SimKey wbest[kReorderThreads / 32];
     __shared__ int32_t s_anchor, s_out, s_next, s_win;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -991,12 +1007,25 @@ __global__ void __launch_bounds__(kReorderThreads) k_local_reorder(
     if (c0 >= m_aic) return;
     const int R = (int)(m_aic - c0 < CR ? m_aic - c0 : CR);
     auto kept = [&](int32_t j) { return tau_col <= 0 || colcount[j] > tau_col; };
-    for (int b = threadIdx.x; b < R; b += blockDim.x) {
+    for (int q = threadIdx.x; q < kReorderHash; q += blockDim.x) head[q] = -1;
+    __syncthreads();
+    // the index: one warp per row, its kept entries pushed on their columns' chains
+    for (int b = warp; b < R; b += blockDim.x >> 5) {
         const int32_t i = aic_in[c0 + b];
-        int32_t c = 0;
-        for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) c += kept(colidx[p]) ? 1 : 0;
-        klen[b] = c;
-        used[b] = 0;
+        const int32_t p0 = rowptr[i], p1 = rowptr[i + 1];
+        int32_t cnt = 0;
+        for (int32_t p = p0 + lane; p < p1; p += 32) {
+            const int32_t c = colidx[p];
+            if (!kept(c)) continue;
+            ++cnt;
+            erow[p] = (int16_t)b;
+            link[p] = atomicExch(&head[col_hash(c)], p);
+        }
+        cnt = warp_sum(cnt);
+        if (lane == 0) {
+            klen[b] = cnt;
+            used[b] = 0;
+        }
     }
     if (threadIdx.x == 0) {
         s_out = 0;
@@ -1014,26 +1043,20 @@ __global__ void __launch_bounds__(kReorderThreads) k_local_reorder(
                 aic_out[c0 + s_out++] = aic_in[c0 + a];
             }
         }
+        for (int b = threadIdx.x; b < R; b += blockDim.x) inter[b] = 0;
         __syncthreads();
         const int a = s_anchor;
         if (a >= R) break;
         const int32_t ia = aic_in[c0 + a];
-        const int32_t pa0 = rowptr[ia], pa1 = rowptr[ia + 1];
-        for (int b = threadIdx.x; b < R; b += blockDim.x) {
-            if (used[b]) continue;
-            const int32_t ib = aic_in[c0 + b];
-            int32_t p = pa0, q = rowptr[ib], q1 = rowptr[ib + 1], cnt = 0;
-            while (p < pa1 && q < q1) {
-                const int32_t ca = colidx[p], cb = colidx[q];
-                if (ca < cb) ++p;
-                else if (ca > cb) ++q;
-                else {
-                    cnt += kept(ca) ? 1 : 0;
-                    ++p;
-                    ++q;
-                }
+        // intersections through the index: each kept column of the anchor walks its chain
+        for (int32_t p = rowptr[ia] + threadIdx.x; p < rowptr[ia + 1]; p += blockDim.x) {
+            const int32_t c = colidx[p];
+            if (!kept(c)) continue;
+            for (int32_t q = head[col_hash(c)]; q >= 0; q = link[q]) {
+                if (colidx[q] != c) continue;  // another column in the same bucket
+                const int b = erow[q];
+                if (!used[b]) atomicAdd(&inter[b], 1);
             }
-            inter[b] = cnt;
         }
         __syncthreads();
         for (int pick = 0; pick < TM - 1; ++pick) {
@@ -1106,12 +1129,16 @@ ns_status_t window_pass(Plan* P, WindowResult* W, cudaStream_t s)
     }
     if (t.reorder > 0 && m_aic > 0) {  // Section 6.1 local reordering of the kept rows
         int32_t* reordered = nullptr;
+        int32_t* link = nullptr;  // the clusters' column indexes, by CSR position
+        int16_t* erow = nullptr;
         Arena ar;
         ar.reserve(&reordered, m_aic);
+        ar.reserve(&link, nnz > 0 ? nnz : 1);
+        ar.reserve(&erow, nnz > 0 ? nnz : 1);
         NS_TRY(ar.commit(s));
         const int CR = t.reorder * TM;
         k_local_reorder<<<(unsigned)ceil_div(m_aic, CR), kReorderThreads, 0, s>>>(
-            P->rowptr, P->colidx, colcount, t.tau_col, aic_rows, m_aic, TM, CR, reordered);
+            P->rowptr, P->colidx, colcount, t.tau_col, aic_rows, m_aic, TM, CR, reordered, link, erow);
         NS_LAUNCH_CHECK();
         NS_CUDA_TRY(cudaMemcpyAsync(aic_rows, reordered, sizeof(int32_t) * m_aic, cudaMemcpyDeviceToDevice, s));
         ar.release(s);

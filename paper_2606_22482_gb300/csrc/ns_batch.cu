@@ -387,10 +387,10 @@ static ns_status_t time_tune(const ns_csr_t* A, int32_t K, ns_dtype_t dt, const 
 // A fresh plan for every execute: the whole cycle (plan, execute, release), best of two, which is
 // what a caller that re-plans every step pays (launch gaps and the release included).
 static ns_status_t time_cycle(const ns_csr_t* A, int32_t K, ns_dtype_t dt, const ns_tune_t& t,
-                              const void* Bd, float* Cd, cudaStream_t st, double* cycle_ms)
+                              const void* Bd, float* Cd, cudaStream_t st, double* cycle_ms, int reps = 2)
 {
     double best = 1e30;
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int rep = 0; rep < reps; ++rep) {
         const double t0 = now_s();
         Plan* P = nullptr;
         NS_TRY(plan_create(A, K, dt, &t, st, &P));
@@ -533,12 +533,18 @@ ns_status_t ns_autotune(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, ns_str
     int trials = 0;
     ns_tune_t best = base;
     double best_cost = 1e300, best_exec = 0;
+    struct Seen {
+        double cost, exec;
+        ns_tune_t t;
+    };
+    std::vector<Seen> seen;  // every candidate with its cost
     auto consider = [&](const ns_tune_t& t, double ex, double pl) {
         double c = ex + pl / amort;
         if (amort <= 1.0) {  // re-planned every execute: time the whole cycle as the caller runs it
             double cyc = 0;
             if (time_cycle(A, K, b_dtype, t, Bd, Cd, st, &cyc) == NS_OK) c = cyc;
         }
+        seen.push_back({c, ex, t});
         ++trials;
         if (c < best_cost) {
             best_cost = c;
@@ -650,6 +656,21 @@ ns_status_t ns_autotune(const ns_csr_t* A, int32_t K, ns_dtype_t b_dtype, ns_str
             else if (r != NS_ERR_UNSUPPORTED) {
                 release();
                 return r;
+            }
+        }
+    }
+    // Re-planned every execute, the whole-cycle times of the leading candidates are close and
+    // noisy: time the three best again, longer, and keep the fastest.
+    if (amort <= 1.0 && seen.size() > 1) {
+        std::stable_sort(seen.begin(), seen.end(), [](const Seen& x, const Seen& y) { return x.cost < y.cost; });
+        double best_c = 1e30;
+        for (size_t k = 0; k < seen.size() && k < 3; ++k) {
+            double cyc = 0;
+            if (time_cycle(A, K, b_dtype, seen[k].t, Bd, Cd, st, &cyc, 6) != NS_OK) continue;
+            if (cyc < best_c) {
+                best_c = cyc;
+                best = seen[k].t;
+                best_exec = seen[k].exec;
             }
         }
     }

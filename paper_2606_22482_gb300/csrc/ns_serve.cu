@@ -89,6 +89,8 @@ struct SReq {
     int32_t* cnt = nullptr;
     int cls = 0;                    // size class: 1 = bulk
     cudaEvent_t done_ev = nullptr;  // recorded after the copy of C to the host
+    const void* hB = nullptr;       // small requests with page-locked B and C: their device
+    float* hC = nullptr;            // mappings, copied by SM loads (NULL: copy engines)
 };
 
 struct Pinned {
@@ -116,6 +118,48 @@ constexpr int kBulkInflight = 2;
 // Host<->device copies go in pieces of at most 4 MB: a copy engine switches between streams at
 // copy boundaries, so a small request's copy waits at most one piece behind a bulk transfer.
 constexpr size_t kCopyPiece = 4u << 20;
+
+// Small requests' copies by SM loads and stores over the host link, when the host buffer is
+// page-locked and mapped: they never queue behind a bulk request's transfer in a copy engine.
+// 16-byte vectors, four in flight per thread, a few CTAs (the bulk launches leave SMs free).
+__global__ void __launch_bounds__(256) k_copy16(uint4* __restrict__ dst, const uint4* __restrict__ src, int64_t n16)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n16; i += 4 * stride) {
+        const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+        dst[i] = a;
+        dst[i + stride] = b;
+        dst[i + 2 * stride] = c;
+        dst[i + 3 * stride] = d;
+    }
+    for (; i < n16; i += stride) dst[i] = src[i];
+}
+
+static void copy_sm(void* dst, const void* src, size_t bytes, cudaStream_t s)
+{
+    const int64_t n16 = (int64_t)(bytes / 16);
+    if (n16 == 0) return;
+    int64_t blocks = (n16 + 4 * 256 - 1) / (4 * 256);
+    if (blocks > 32) blocks = 32;
+    k_copy16<<<(unsigned)blocks, 256, 0, s>>>(static_cast<uint4*>(dst), static_cast<const uint4*>(src), n16);
+    count_launch();
+    (void)cudaGetLastError();
+}
+
+// the device address of a page-locked, mapped host buffer (16-byte aligned), else NULL
+static void* mapped(const void* h)
+{
+    if (!h || (reinterpret_cast<uintptr_t>(h) & 15u)) return nullptr;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    if (reinterpret_cast<uintptr_t>(at.devicePointer) & 15u) return nullptr;
+    return at.devicePointer;
+}
 
 static void copy_pieces(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s)
 {
@@ -433,6 +477,16 @@ static void prepare(Server* S, std::vector<SReq*>& fresh, std::vector<SReq*>& re
         }
         q->block = blk;
         q->dB = blk;
+        q->hB = nullptr;
+        q->hC = nullptr;
+        if (q->cls == 0 && bB % 16 == 0 && bC % 16 == 0) {  // both mapped, or neither is used
+            const void* mb = g.n > 0 ? mapped(q->r.B) : nullptr;
+            void* mc = g.m > 0 ? mapped(q->r.C) : nullptr;
+            if (mb && mc) {
+                q->hB = mb;
+                q->hC = static_cast<float*>(mc);
+            }
+        }
         q->dC = reinterpret_cast<float*>(static_cast<char*>(blk) + bB);
         q->slots = reinterpret_cast<float*>(static_cast<char*>(blk) + bB + bC);
         q->cnt = reinterpret_cast<int32_t*>(static_cast<char*>(blk) + bB + bC + bS);
@@ -495,7 +549,10 @@ static void launch_group(Server* S, std::vector<SReq*>& rs, int cls, int K, bool
     for (SReq* q : rs) {
         const SGraph& g = S->graphs[q->r.graph_id];
         const size_t eb = q->r.b_dtype == NS_BF16 ? 2 : 4;
-        if (g.n > 0) copy_pieces(q->dB, q->r.B, (size_t)g.n * q->r.K * eb, cudaMemcpyHostToDevice, cs);
+        if (g.n > 0) {
+            if (q->hB) copy_sm(q->dB, q->hB, (size_t)g.n * q->r.K * eb, cs);
+            else copy_pieces(q->dB, q->r.B, (size_t)g.n * q->r.K * eb, cudaMemcpyHostToDevice, cs);
+        }
     }
     cudaEventCreate(&L.h2d_ev);
     cudaEventRecord(L.h2d_ev, cs);
@@ -537,8 +594,10 @@ static void launch_group(Server* S, std::vector<SReq*>& rs, int cls, int K, bool
     for (SReq* q : order) {
         const SGraph& g = S->graphs[q->r.graph_id];
         q->st.t_start = t_start;
-        if (r == NS_OK && g.m > 0)
-            copy_pieces(q->r.C, q->dC, (size_t)g.m * q->r.K * 4, cudaMemcpyDeviceToHost, es);
+        if (r == NS_OK && g.m > 0) {
+            if (q->hC) copy_sm(q->hC, q->dC, (size_t)g.m * q->r.K * 4, es);
+            else copy_pieces(q->r.C, q->dC, (size_t)g.m * q->r.K * 4, cudaMemcpyDeviceToHost, es);
+        }
         cudaEventCreate(&q->done_ev);
         cudaEventRecord(q->done_ev, es);
     }

@@ -136,7 +136,9 @@ class ClockSampler:
 EXEC_SOURCES = ("ns_exec.cu", "ns_internal.cuh", "ns_dense.cuh", "ns_dense_tc.cuh", "ns_ptx.cuh")
 MEASURED_TRAFFIC = {
     # (workload, tau_tile, chunk_nnz, l2_hints): (source digest, bytes per launch)
-    ("powerlaw", 2147483647, 512, 1): ("6f9a93d7e3bfe374", 1677244416 + 541765120),
+    ("powerlaw", 2147483647, 512, 1): ("ce2d73446f053432", 1676767488 + 542345216),
+    ("powerlaw", 2147483647, 256, 1): ("ce2d73446f053432", 1699133952 + 585530112),
+    ("powerlaw", 2147483647, 512, 2): ("ce2d73446f053432", 1520246272 + 536258048),
 }
 
 

@@ -973,14 +973,18 @@ __device__ __forceinline__ void contig_chunk(const ExecDesc& D, int32_t c, int l
 }
 
 // SMEM_RING: the FP32 one-vector form may stage its gathers in the shared-memory cp.async ring
-// (pays off when the gathered rows come from DRAM; when B sits in L2 the register ring is faster)
-template <int VPL, int EPS, bool BF16, bool HINT, bool SMEM_RING = true>
+// (pays off when the gathered rows come from DRAM; when B sits in L2 the register ring is faster).
+// HOTMAP: that ring form is built twice, with and without the planner's hot-row map, so the common
+// build carries no registers for the map (the map is a cache hint only: a build without it ignores
+// it and computes the same C); the register-ring forms read the map whenever a plan has one.
+template <int VPL, int EPS, bool BF16, bool HINT, bool SMEM_RING = true, bool HOTMAP = false>
 __global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : (EPS == 2 ? 6 : 5)) k_exec_contig(
     const ExecDesc* __restrict__ descs, const int32_t* __restrict__ queue,
     const int32_t* __restrict__ queue_desc, int64_t n_items, int32_t* ctrl,
     const __grid_constant__ ExecDesc d0)
 {
     constexpr bool ASYNC = SMEM_RING && VPL == 1 && EPS == 1 && !BF16;
+    constexpr bool READ_HOT = HINT && (!ASYNC || HOTMAP);
     __shared__ float4 s_park[kExecWarps * 32 * VPL];  // one parked partial row per warp
     __shared__ float4 s_aring[ASYNC ? kExecWarps * 8 * 32 : 1];
     __shared__ int2 s_bat[kExecWarps * 128];          // per warp: 4 batches of 32 (col, value)
@@ -1008,9 +1012,9 @@ __global__ void __launch_bounds__(kExecThreads, VPL == 1 ? 8 : (EPS == 2 ? 6 : 5
         }
         const bool full = D.K == 128 / EPS * VPL;
         float4* const aring = s_aring + (ASYNC ? (threadIdx.x >> 5) * 8 * 32 : 0);
-        if (HINT && D.hot) {
-            if (full) contig_chunk<VPL, EPS, BF16, HINT, true, HINT, false>(D, (int32_t)c, lane, pol, park, bat, aring);
-            else contig_chunk<VPL, EPS, BF16, HINT, false, HINT, false>(D, (int32_t)c, lane, pol, park, bat, aring);
+        if (READ_HOT && D.hot) {
+            if (full) contig_chunk<VPL, EPS, BF16, HINT, true, HINT, ASYNC>(D, (int32_t)c, lane, pol, park, bat, aring);
+            else contig_chunk<VPL, EPS, BF16, HINT, false, HINT, ASYNC>(D, (int32_t)c, lane, pol, park, bat, aring);
         } else {
             if (full) contig_chunk<VPL, EPS, BF16, HINT, true, false, ASYNC>(D, (int32_t)c, lane, pol, park, bat, aring);
             else contig_chunk<VPL, EPS, BF16, HINT, false, false, ASYNC>(D, (int32_t)c, lane, pol, park, bat, aring);
@@ -1107,7 +1111,7 @@ static ExecKernel pick_kernel(int K)
 
 // nonzeros per warp step: as many lane groups as the K/4 vectors of a row leave room for
 template <bool BF16, bool HINT>
-static ExecKernel pick_contig(int K, bool b_in_l2)
+static ExecKernel pick_contig(int K, bool b_in_l2, bool hot)
 {
     if (K <= 32) return k_exec_contig<1, 4, BF16, HINT>;
     if (K <= 64) return k_exec_contig<1, 2, BF16, HINT>;
@@ -1116,18 +1120,23 @@ static ExecKernel pick_contig(int K, bool b_in_l2)
     } else {
         if (K <= 128 && b_in_l2) return k_exec_contig<1, 1, BF16, HINT, false>;
     }
-    if (K <= 128) return k_exec_contig<1, 1, BF16, HINT>;
+    if (K <= 128) {
+        if constexpr (!BF16 && HINT)
+            if (hot) return k_exec_contig<1, 1, BF16, HINT, true, true>;
+        return k_exec_contig<1, 1, BF16, HINT>;
+    }
     return k_exec_contig<2, 1, BF16, HINT>;
 }
 
 // contig: 0, or a residual-only launch whose plans all have a contiguous residual stream
-// (K <= 256): kContig, or kContigBInL2 when B fits comfortably in L2
+// (K <= 256): kContig, kContigBInL2 when B fits comfortably in L2, or kContigHot for a single
+// plan with a hot-row map
 static ExecKernel select_kernel(int K, bool bf16, bool hint, bool dense, int contig)
 {
     if (contig && !dense && K <= 256) {
-        const bool in_l2 = contig == kContigBInL2;
-        if (bf16) return hint ? pick_contig<true, true>(K, in_l2) : pick_contig<true, false>(K, in_l2);
-        return hint ? pick_contig<false, true>(K, in_l2) : pick_contig<false, false>(K, in_l2);
+        const bool in_l2 = contig == kContigBInL2, hot = contig == kContigHot;
+        if (bf16) return hint ? pick_contig<true, true>(K, in_l2, hot) : pick_contig<true, false>(K, in_l2, hot);
+        return hint ? pick_contig<false, true>(K, in_l2, hot) : pick_contig<false, false>(K, in_l2, hot);
     }
     if (bf16) {
         if (hint) return dense ? pick_kernel<true, true, true>(K) : pick_kernel<true, true, false>(K);
@@ -1249,7 +1258,7 @@ ns_status_t exec_launch_plan(Plan* P, cudaStream_t s)
     if (plan_contig(P)) {
         // B (this slice of it) within half of L2: the gathers hit L2, keep them in registers
         const int64_t b_bytes = P->st.n * (int64_t)K * (P->dtype == NS_BF16 ? 2 : 4);
-        contig = 2 * b_bytes <= l2_bytes(P->device) ? kContigBInL2 : kContig;
+        contig = 2 * b_bytes <= l2_bytes(P->device) ? kContigBInL2 : (P->hot_bits ? kContigHot : kContig);
     }
     return exec_launch(nullptr, P->queue, nullptr, P->st.n_items, P->ctrl, K, P->tune.TM,
                        P->tune.TK, P->dtype == NS_BF16, P->tune.l2_hints != 0, P->st.n_dwin > 0,

@@ -231,6 +231,7 @@ int64_t l2_bytes(int device);
 // residual-only launch modes of exec_launch / exec_prepare (`contig`)
 constexpr int kContig = 1;       // contiguous residual stream
 constexpr int kContigBInL2 = 2;  // the same, with B small enough to stay in L2
+constexpr int kContigHot = 3;    // kContig, single plan with a hot-row map (l2_hints = 2)
 
 // planner entry (ns_plan.cu)
 ns_status_t plan_build(Plan* P, const ns_csr_t* A, int32_t K, ns_dtype_t dt, const ns_tune_t* tune,

@@ -109,11 +109,12 @@ struct SLaunch {
 };
 
 constexpr int64_t kBulkBytes = 32ll << 20;  // B + C above this: the bulk size class
-// Bulk requests admitted at once.  The copy engines take copies in arrival order whatever their
-// stream, so bulk transfers queued ahead of a small request's copies delay it by their whole
-// length; with at most this many bulk requests in flight that delay stays a few milliseconds,
-// and bulk requests wait in the queue instead (small ones pass them).
-constexpr int kBulkInflight = 2;
+// Bulk requests admitted at once (small ones pass waiting bulk ones).  The copy engines take
+// copies in arrival order whatever their stream, so bulk transfers queued ahead of another copy
+// delay it by their whole length; small requests with mapped host buffers use no copy engine at
+// all (SM copies for B, C, counters and the launch's staging), so this cap only bounds how long
+// a bulk request's own copies wait behind earlier bulk transfers.
+constexpr int kBulkInflight = 8;
 
 // Host<->device copies go in pieces of at most 4 MB: a copy engine switches between streams at
 // copy boundaries, so a small request's copy waits at most one piece behind a bulk transfer.
@@ -194,6 +195,7 @@ struct Server {
     std::multimap<size_t, void*> dev_free;  // device blocks whose last use has completed (worker)
     cudaEvent_t ref_ev = nullptr;  // GPU time origin: completed at server clock t_ref
     void* zeros = nullptr;         // pinned zeros: split counters are cleared by a copy, not a kernel
+    const void* zeros_dev = nullptr;  // their device address when mapped (SM copies), else NULL
     size_t zeros_bytes = 0;
     double t_ref = 0;
     size_t dev_cached = 0;
@@ -491,8 +493,12 @@ static void prepare(Server* S, std::vector<SReq*>& fresh, std::vector<SReq*>& re
         q->slots = reinterpret_cast<float*>(static_cast<char*>(blk) + bB + bC);
         q->cnt = reinterpret_cast<int32_t*>(static_cast<char*>(blk) + bB + bC + bS);
         // split-row arrival counters start at zero: a copy from pinned zeros keeps the copy stream
-        // off the SMs (a memset is a kernel, which would wait behind running SpMM launches)
-        if (bN <= S->zeros_bytes) cudaMemcpyAsync(q->cnt, S->zeros, bN, cudaMemcpyHostToDevice, S->s_copy[q->cls]);
+        // off the SMs (a memset is a kernel, which would wait behind running SpMM launches).  A
+        // request whose B and C move by SM copies clears them by an SM copy too: the copy engines
+        // take copies in arrival order, so even this small copy would wait behind every piece of
+        // a bulk transfer queued before it.
+        if (q->hB && S->zeros_dev && bN <= S->zeros_bytes) copy_sm(q->cnt, S->zeros_dev, bN, S->s_copy[q->cls]);
+        else if (bN <= S->zeros_bytes) cudaMemcpyAsync(q->cnt, S->zeros, bN, cudaMemcpyHostToDevice, S->s_copy[q->cls]);
         else cudaMemsetAsync(q->cnt, 0, bN, S->s_copy[q->cls]);
         ready.push_back(q);
     }
@@ -566,7 +572,10 @@ static void launch_group(Server* S, std::vector<SReq*>& rs, int cls, int K, bool
     }
     std::memset(h + bD + 2 * bQ, 0, 256);  // ctrl: work ticket and status
     char* base = static_cast<char*>(block);
-    cudaMemcpyAsync(base, h, total, cudaMemcpyHostToDevice, es);
+    // the launch's descriptors and work list: by an SM copy when the staging is mapped (a copy
+    // engine would queue it behind every bulk piece issued before it), else by a copy engine
+    if (const void* hm = mapped(h)) copy_sm(base, hm, total, es);
+    else cudaMemcpyAsync(base, h, total, cudaMemcpyHostToDevice, es);
     cudaEventCreateWithFlags(&L.up_ev, cudaEventDisableTiming);
     cudaEventRecord(L.up_ev, es);
     cudaStreamWaitEvent(es, L.h2d_ev, 0);
@@ -751,6 +760,7 @@ ns_status_t ns_serve_create(const ns_serve_cfg_t* cfg, ns_server_t* out)
     S->zeros_bytes = 1 << 20;
     NS_CUDA_TRY(cudaHostAlloc(&S->zeros, S->zeros_bytes, cudaHostAllocDefault));
     std::memset(S->zeros, 0, S->zeros_bytes);
+    S->zeros_dev = mapped(S->zeros);
     NS_CUDA_TRY(cudaEventCreate(&S->ref_ev));
     NS_CUDA_TRY(cudaEventRecord(S->ref_ev, S->s_exec[0][0]));
     NS_CUDA_TRY(cudaEventSynchronize(S->ref_ev));

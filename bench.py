@@ -139,6 +139,7 @@ MEASURED_TRAFFIC = {
     ("powerlaw", 2147483647, 512, 1): ("ce2d73446f053432", 1676767488 + 542345216),
     ("powerlaw", 2147483647, 256, 1): ("ce2d73446f053432", 1699133952 + 585530112),
     ("powerlaw", 2147483647, 512, 2): ("ce2d73446f053432", 1520246272 + 536258048),
+    ("powerlaw", 2147483647, 1024, 1): ("ce2d73446f053432", 1670158080 + 531273984),
 }
 
 

@@ -44,6 +44,17 @@ def test_rebalance_loop(which, dtype):
         assert tc >= 0 and res >= 0 and max(tc, res) > 0
     # bisection: the visited taus never repeat
     assert len(set(rep["tau"])) == len(rep["tau"])
+    # the loop keeps the threshold of the epoch that finished first (span = the later class's end)
+    spans = [max(a, b) for a, b in zip(rep["dt_tc_ms"], rep["dt_res_ms"])]
+    assert t.tau_tile == rep["tau"][int(np.argmin(spans))]
+    # Eq. 6: converged exactly when some epoch's two classes ended within 1 + eps of each other
+    # (a class with no work gives an unbounded skew); a small margin absorbs the eps rounding
+    ratios = [max(a, b) / min(a, b) if min(a, b) > 0 else float("inf")
+              for a, b in zip(rep["dt_tc_ms"], rep["dt_res_ms"])]
+    if rep["converged"]:
+        assert min(ratios) <= 1.05 + 1e-6
+    else:
+        assert min(ratios) > 1.05 - 1e-6
     tol = 2e-2 if dtype == ns.NS_BF16 else 1e-5
     ref = oracle.spmm(A, Bh, b_bf16=dtype == ns.NS_BF16)
     assert oracle.rel_frobenius(C.cpu().numpy(), ref) <= tol

@@ -14,9 +14,12 @@ is needed between steps.
              CUDA-event duration, against the measured HBM copy bandwidth
   e2e        the same metric through ns_spmm_host with pinned host buffers (H2D of A and B,
              plan, execute, D2H of C inside the timed region)
-  cpu_baseline  the FP64 oracle on a bounded row sample of the same workload, host cores
+  cpu_baseline  the FP64 oracle on the host cores over the whole matrix (about 0.2 s on 16
+             cores for the power-law graph; larger workloads take a bounded row sample), with a
+             single-thread figure and the CPU model
 
---impl reference runs the oracle (the reference arm of this build) on the same workload.
+--impl reference runs the oracle (the reference arm of this build) on the same workload, the
+whole matrix every step, and prints the same metric.
 With --gpus N > 1 (torchrun) every rank runs an independent replica (the path needs no
 exchange); value sums the replicas' work over the slowest rank's time.
 """

@@ -27,6 +27,10 @@ def test_reference_arm_json_line():
     assert line["unit"] == "GFLOP/s" and line["value"] > 0 and line["higher_is_better"] is True
     assert line["steps"] == 1 and line["warmup"] == 0 and line["n_gpus"] == 1
     assert line["config"]["workload"].startswith("powerlaw-rmat-2^20")
+    # the power-law configuration at its full size: 2^20 x 2^20, 2^24 distinct edges, K = 128
+    cfg = line["config"]
+    assert cfg["m"] == cfg["n"] == 1 << 20 and cfg["nnz"] == 1 << 24 and cfg["K"] == 128
+    assert cfg["b_dtype"] == "f32"
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     e2e = line["e2e"]
